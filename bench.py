@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput and latency of the incremental-SVD update stream on one GB300 (or N replicas).
+
+Workload (default): one FP32-bulk stream started from a 2,000 x 1,000 factor-model panel
+(20 factors, Student-t noise), k = 64, mixed updates 70% row appends / 10% column appends /
+20% rank-1 entry updates (delta sd 0.005), error-threshold refresh (ratio > 1.05) and
+angle-threshold refresh (largest principal angle to the optimal subspace > 5 degrees) checked
+every 250 updates, loss-of-orthogonality monitor every 256 updates. A "step" is one batch of
+``--batch`` consecutive events of that stream through the whole path (projection, core SVD,
+rotations, dense-A bookkeeping, policy checks, refreshes, re-orthogonalisation).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on the same stream.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2605_24514_gb300 import streams  # noqa: E402
+
+WORKLOADS = {
+    "panel-2000x1000-k64": dict(prec="fp32", check_every=250, gamma=1.05, theta_deg=5.0, batch=500,
+                                desc="2000x1000 factor panel (20 factors, t4 noise), k=64, 70/10/20 row/col/entry, "
+                                     "FP32 bulk + FP64 core/rho/sigma, refresh on ratio>1.05 or angle>5deg"),
+    "panel-200x50-k10": dict(prec="fp64", check_every=50, T_refresh=250, batch=200,
+                             desc="200x50 factor panel (5 factors), k=10, 1000 row appends then 200 entry "
+                                  "updates, FP64, periodic refresh 250, metrics every 50"),
+}
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return HBM_PEAK_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_stream(name, seed, n_events):
+    A0, ev, k, extra = streams.workload(name, seed=seed, n_events=n_events)
+    return A0, ev, k
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_2605_24514_gb300 as pkg
+    from paper_2605_24514_gb300 import build as b
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    W = WORKLOADS[args.workload]
+    B = args.batch or W["batch"]
+    K, Wm = args.steps, args.warmup
+    n_ev = (Wm + 2 * K) * B
+    A0, ev, k = make_stream(args.workload, seed=rank, n_events=n_ev)
+    prec = pkg.FP32 if W["prec"] == "fp32" else pkg.FP64
+    dt = np.float32 if prec == pkg.FP32 else np.float64
+    st = torch.cuda.Stream()
+    g = pkg.ISVD(A0, k, prec=prec, k_max=k, stream=st.cuda_stream, seed=rank)
+    if "gamma" in W:
+        g.set_policy(kind=pkg.POLICY_ERROR | pkg.POLICY_ANGLE, check_every=W["check_every"], gamma=W["gamma"],
+                     theta_max=np.deg2rad(W["theta_deg"]))
+    else:
+        g.set_policy(kind=pkg.POLICY_PERIODIC, T_refresh=W["T_refresh"], check_every=W["check_every"])
+    payload = torch.from_numpy(ev.payload.astype(dt)).to("cuda")   # resident in HBM
+    slices = []
+    for s in range(Wm + 2 * K):
+        a, e = s * B, (s + 1) * B
+        sl = ev.slice(a, e)
+        base = int(ev.off[a]) if e > a else 0
+        slices.append((sl, base, base + sl.payload.size))
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+
+    def step_dev(i):
+        sl, lo, hi = slices[i]
+        g.apply_events(sl, payload=payload[lo:hi])
+
+    for i in range(Wm):
+        step_dev(i)
+    g.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    g.profile(True)
+    l0 = g.launches
+    ratios = []
+    clocks.start()
+    evs = []
+    for i in range(Wm, Wm + K):
+        flush.zero_()                       # evict L2 (129 MB) between steps, outside the timing
+        st.wait_stream(torch.cuda.current_stream())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step_dev(i)
+        e1.record(st)
+        evs.append((e0, e1))
+        ratios.append(g.last_check_metrics()["frob_ratio"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = g.launches - l0
+    ms = sum(a.elapsed_time(b_) for a, b_ in evs)
+    prof = g.profile_read()
+    lat = g.latencies_us()
+    g.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * K * B / (ms / 1e3)
+
+    # End to end through the public API with host buffers: each step copies its payload from
+    # pinned host memory and reads sigma back.
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for i in range(Wm + K, Wm + 2 * K):
+            sl, lo, hi = slices[i]
+            h = torch.empty(hi - lo, dtype=torch.float32 if dt == np.float32 else torch.float64).pin_memory()
+            h.copy_(torch.from_numpy(ev.payload[lo:hi].astype(dt)))
+            pinned.append(h)
+        g.sync()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for j, i in enumerate(range(Wm + K, Wm + 2 * K)):
+            sl, lo, hi = slices[i]
+            g.apply_events(sl, payload=pinned[j].numpy())
+            sig = g.sigma()
+            h2d += pinned[j].numel() * pinned[j].element_size() + 48 * len(sl)
+            d2h += sig.nbytes
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * K * B / el, "unit": "updates/s", "h2d_bytes_per_step": int(h2d // K),
+               "d2h_bytes_per_step": int(d2h // K)}
+
+    if rank != 0:
+        return None
+    peak, peak_src = measured_peaks()
+    # Dominant kernel class by device time; HBM roofline from algorithmic bytes / its time.
+    dom = max(prof, key=lambda c: prof[c][0])
+    rot_ms, rot_bytes, rot_n = prof["rotate"]
+    classes = {c: {"ms": round(v[0], 3), "launches": int(v[2]),
+                   "us_per_launch": round(1e3 * v[0] / v[2], 3) if v[2] else None,
+                   "GBps": round(v[1] / (v[0] * 1e6), 1) if v[0] > 0 and v[1] > 0 else None}
+               for c, v in prof.items()}
+    roof_cls = dom if prof[dom][1] > 0 else "rotate"
+    r_ms, r_bytes, r_n = prof[roof_cls]
+    achieved = r_bytes / (r_ms * 1e6) if r_ms > 0 else 0.0
+    out = {
+        "metric": "iSVD updates/s and p50/p99 update latency at err ratio<=1.05 vs plain GPU form",
+        "value": round(value, 1),
+        "unit": "updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": round(ms / K, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == pkg.FP32 else "f64",
+        "data": "synthetic (seeded factor-model panel and update stream)",
+        "config": {"workload": args.workload, "desc": W["desc"], "events_per_step": B,
+                   "m_n_end": [int(ev.m_after[(Wm + K) * B - 1]), int(ev.n_after[(Wm + K) * B - 1])],
+                   "form": "per-update kernel launches on one CUDA stream (no graph, no batching)",
+                   "l2": "flushed between steps (256 MB device write, untimed)",
+                   "latency_us": {"p50": round(float(np.percentile(lat, 50)), 2),
+                                  "p99": round(float(np.percentile(lat, 99)), 2),
+                                  "mean": round(float(np.mean(lat)), 2), "n": int(lat.size)},
+                   "err_ratio_at_checks_max": (None if not np.isfinite(np.nanmax(ratios)) else
+                                               round(float(np.nanmax(ratios)), 5)) if ratios else None,
+                   "kernel_classes": classes,
+                   "parallelism": "replicas" if world > 1 else "single stream"},
+        "roofline": {"kernel": roof_cls, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                     "dominant_class": dom},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+    return out
+
+
+def oracle_policy(W):
+    import oracle
+    if "gamma" in W:
+        return oracle.Policy(kind=oracle.POLICY_ERROR | oracle.POLICY_ANGLE, check_every=W["check_every"],
+                             gamma=W["gamma"], theta_max=np.deg2rad(W["theta_deg"]))
+    return oracle.Policy(kind=oracle.POLICY_PERIODIC, T_refresh=W["T_refresh"], check_every=W["check_every"])
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """The oracle (as it stands) on a time-bounded prefix of the same stream."""
+    import oracle
+    W = WORKLOADS[args.workload]
+    A0, ev, k = make_stream(args.workload, seed=0, n_events=4000)
+    dt = np.float32 if W["prec"] == "fp32" else np.float64
+    o = oracle.OracleISVD(A0.astype(dt).astype(np.float64), k, tol_rel=3e-6 if dt == np.float32 else 1e-10,
+                          policy=oracle_policy(W))
+    t0 = time.perf_counter()
+    n = 0
+    while n < len(ev) and time.perf_counter() - t0 < budget_s:
+        kd = int(ev.kind[n])
+        if kd == oracle.ENTRY:
+            o.update_entry(ev.i[n], ev.j[n], ev.delta[n])
+        else:
+            o.apply(kd, ev.vector(n).astype(dt).astype(np.float64))
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": round(n / el, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"first {n} events of the same stream (time budget {budget_s:.0f} s, policy checks included)"}
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return int(max(th))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args):
+    """The oracle timed per step on a bounded sample of the same workload."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    import oracle
+    W = WORKLOADS[args.workload]
+    Bref = args.ref_batch
+    n_ev = (args.warmup + args.steps) * Bref
+    A0, ev, k = make_stream(args.workload, seed=0, n_events=n_ev)
+    dt = np.float32 if W["prec"] == "fp32" else np.float64
+    o = oracle.OracleISVD(A0.astype(dt).astype(np.float64), k, tol_rel=3e-6 if dt == np.float32 else 1e-10,
+                          policy=oracle_policy(W))
+
+    def step(s):
+        for e in range(s * Bref, (s + 1) * Bref):
+            kd = int(ev.kind[e])
+            if kd == oracle.ENTRY:
+                o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+            else:
+                o.apply(kd, ev.vector(e).astype(dt).astype(np.float64))
+
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        step(s)
+    el = time.perf_counter() - t0
+    value = args.steps * Bref / el
+    cores = _blas_threads()
+    sample = f"{Bref} events per step of the same stream, events {args.warmup * Bref}..{n_ev - 1}"
+    return {"impl": "reference", "metric": "iSVD updates/s and p50/p99 update latency at err ratio<=1.05 vs plain GPU form",
+            "value": round(value, 3), "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded factor-model panel and update stream)",
+            "config": {"workload": args.workload, "desc": W["desc"], "events_per_step": Bref},
+            "cpu_baseline": {"value": round(value, 3), "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="panel-2000x1000-k64", choices=list(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--ref-batch", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * isvd.h — C ABI of libisvd, a GB300 (sm_103a) engine for the Brand-style incremental SVD
+ * of arXiv 2605.24514 ("Incremental SVD for Large-Scale Dynamic Matrices").
+ *
+ * The engine maintains A_t ~= U_t diag(sigma_t) V_t^T for a dense matrix A_t that changes by
+ * row appends, column appends and single-entry increments (Section 2.1), refreshes the
+ * factorisation from the stored A_t on demand or by policy (Sections 2.4 and 3), and reports
+ * the error-ratio, principal-angle and EVR metrics of Section 2.5.
+ *
+ * Conventions shared by every call
+ *  - All matrices are ROW-MAJOR. A caller buffer for U holds m*r elements with row stride r,
+ *    V holds n*r elements with row stride r; sigma is r doubles in descending order.
+ *  - The element type of U, V, A and of appended rows/columns is the handle's storage type:
+ *    double for ISVD_FP64, float for ISVD_FP32. sigma, rho, N_t and all metrics are double.
+ *  - "on_device" / "to_device" flags say whether a pointer is CUDA device memory (on the
+ *    handle's device) or host memory. Device pointers must stay valid until the call's work has
+ *    finished on the handle's stream (isvd_sync); host pointers are only read during the call.
+ *  - Ownership: every input is copied into the handle; the caller keeps its buffers. Outputs
+ *    go into caller-allocated buffers. The handle owns all of its device memory.
+ *  - Errors: every call returns an isvd_status and never aborts. Argument errors (bad shape,
+ *    out-of-range index, NaN/Inf in a host input) are detected before any work is queued and
+ *    leave the state unchanged. Device-side failures (core SVD not converged, non-finite data
+ *    seen in a device input) are sticky: they are reported by the next call that synchronises
+ *    (isvd_sync, isvd_metrics, isvd_get_*), and every later call returns the same status.
+ *    isvd_last_error gives a one-line message.
+ *  - Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef ISVD_H_
+#define ISVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isvd_ctx* isvd_t;
+
+typedef enum {
+  ISVD_FP64 = 0,  /* U, V, A and the core SVD in FP64 */
+  ISVD_FP32 = 1   /* U, V, A in FP32; sigma, rho, N_t and the core's singular values in FP64 */
+} isvd_precision;
+
+typedef enum {
+  ISVD_OK = 0,
+  ISVD_EINVAL = 1,      /* bad argument (NULL handle, k < 1, unknown flag, ...) */
+  ISVD_ESHAPE = 2,      /* vector length does not match the current shape */
+  ISVD_EBOUNDS = 3,     /* (i, j) outside the current matrix */
+  ISVD_ENOMEM = 4,      /* device allocation failed */
+  ISVD_EBUDGET = 5,     /* pool admission refused: memory budget or slot count exceeded */
+  ISVD_ENOTCONV = 6,    /* a core Jacobi SVD did not converge within its sweep limit */
+  ISVD_ETIMEOUT = 7,    /* a bounded device-side wait gave up */
+  ISVD_ECUDA = 8,       /* a CUDA runtime call failed */
+  ISVD_ENONFINITE = 9   /* NaN or Inf in an input */
+} isvd_status;
+
+typedef struct {
+  int32_t prec;        /* isvd_precision */
+  int32_t k_max;       /* column capacity of U and V (>= k); 0 means k */
+  double tol_rel;      /* rank test of Section 2.2: a new direction is kept iff
+                          rho > tol_rel * ||x||; <= 0 selects 1e-10 (FP64) or 3e-6 (FP32) */
+  int64_t row_cap;     /* initial row capacity of A and U (0: 2*m0) */
+  int64_t col_cap;     /* initial column capacity of A and row capacity of V (0: 2*n0) */
+  void* cuda_stream;   /* cudaStream_t all work is queued on; NULL = legacy default stream */
+  uint64_t seed;       /* seed of the randomized refresh's test matrix */
+  double orth_tol;     /* re-orthogonalisation trigger on max|U^T U - I|, max|V^T V - I|;
+                          <= 0 selects 1e-5 (FP32) or 1e-12 (FP64) */
+  int64_t orth_every;  /* monitor cadence in updates; 0 selects 256 (FP32) / never (FP64) */
+  int32_t rsvd_oversample;   /* randomized refresh (min(m, n) > 128): extra sketch columns p,
+                                sketch size l = min(k + p, 128); <= 0 selects 16 */
+  int32_t rsvd_power_iters;  /* randomized refresh: power iterations q; < 0 selects 2 */
+} isvd_config;
+
+/* Policy kinds (bit set), Section 3. */
+#define ISVD_POLICY_NONE 0
+#define ISVD_POLICY_PERIODIC 1       /* refresh iff t mod T_refresh == 0, Eq. (periodic-refresh-rule) */
+#define ISVD_POLICY_ERROR 2          /* refresh iff frob_ratio > gamma (and t - t_last >= T_min),
+                                        Eq. (error-refresh-rule) */
+#define ISVD_POLICY_ANGLE 4          /* refresh iff angle_to_opt > theta_max (Section 3.3) */
+#define ISVD_POLICY_ADAPTIVE_RANK 8  /* k <- min(k + 1, k_max) while EVR < tau_evr at a check,
+                                        Eq. (evr-rank-rule) read as a growth rule */
+
+typedef struct {
+  int32_t kind;                    /* bit set of ISVD_POLICY_* */
+  int32_t k_min, k_max;            /* adaptive-rank bounds (k_max <= config k_max) */
+  int32_t store_initial_subspace;  /* refresh also sets U_ref <- U_t (Section 2.4) */
+  int64_t T_refresh;               /* periodic period */
+  int64_t T_min;                   /* minimum spacing of error/angle refreshes */
+  int64_t check_every;             /* cadence of the error/angle/EVR checks (0: never) */
+  double gamma;                    /* error-ratio threshold */
+  double theta_max_rad;            /* angle threshold in radians */
+  double tau_evr;                  /* EVR target */
+} isvd_policy;
+
+/* Metrics of Section 2.5 (names follow the paper). */
+typedef struct {
+  int64_t t, m, n;       /* updates applied, current shape */
+  int32_t r, k;          /* maintained rank, working rank k_t */
+  double frob_error;     /* E_inc = ||A_t - U S V^T||_F */
+  double frob_opt;       /* E_opt = error of the best rank-r approximation */
+  double frob_gap;       /* E_inc - E_opt */
+  double frob_ratio;     /* E_inc / E_opt, NaN when E_opt is numerically zero */
+  double angle;          /* theta_max(U_ref, U_t), Eq. (angle-metrics-ref) */
+  double angle_to_opt;   /* theta_max(U_opt, U_t), Eq. (angle-metrics-opt) */
+  double evr;            /* sum sigma^2 / N_t, Eq. (evr) */
+  double rho_last;       /* residual norm of the last append, Eq. (row-residual) */
+  double novelty_last;   /* rho / ||x|| of the last append (Section 3.3) */
+  double orth_err_u;     /* max |U^T U - I| (measured by the last monitor run) */
+  double orth_err_v;     /* max |V^T V - I| */
+  double N;              /* N_t = ||A_t||_F^2 maintained incrementally (Section 2.4) */
+  int64_t refreshes;     /* refreshes performed */
+  int64_t reorths;       /* re-orthogonalisations performed */
+  int64_t t_last;        /* time of the last refresh */
+} isvd_metrics_t;
+
+/* Flags of isvd_metrics. */
+#define ISVD_METRICS_CHEAP 0  /* t, shape, EVR, N, rho/novelty: no pass over A */
+#define ISVD_METRICS_FULL 1   /* also E_inc, E_opt, ratio, gap and both angles (one pass to
+                                 form E_inc and one truncated SVD of A_t) */
+
+/* One update event for isvd_apply_events. kind: 0 row append, 1 column append, 2 entry. */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  int64_t i, j;    /* entry position (kind 2) */
+  double delta;    /* entry increment (kind 2) */
+  int64_t off;     /* payload offset in elements (kinds 0, 1) */
+  int64_t len;     /* payload length: n for a row, m for a column */
+} isvd_event;
+
+/* --- single-stream engine ------------------------------------------------------------ */
+
+/* Algorithm 1 (initialisation) and Section 2.4: (U, S, V) <- TruncatedSVD(A0, k) at rank
+ * r0 = min(k, m0, n0); A <- A0; N_0 = ||A0||_F^2; U_ref <- U_0; t = 0.
+ * A0 is m0 x n0 row-major with row stride lda (>= n0), host or device memory.
+ * TruncatedSVD is exact (Gram matrix of the short side, Jacobi eigensolver) when
+ * min(m, n) <= 128 and randomized (Halko-Martinsson-Tropp sketch with power iterations)
+ * otherwise; refreshes and the metrics' optimal factorisation use the same routine. */
+isvd_status isvd_create(const isvd_config* cfg, const void* A0, int64_t m0, int64_t n0,
+                        int64_t lda, int k, int a0_on_device, isvd_t* out);
+void isvd_destroy(isvd_t h);
+
+/* As isvd_create, but the initial factors are supplied by the caller instead of computed:
+ * U0 (m0 x r0), sigma0 (r0, descending) and V0 (n0 x r0), row-major with row stride r0, in the
+ * same memory space as A0; r0 must equal min(k, m0, n0). U0 and V0 should have orthonormal
+ * columns. Used to resume a stream from stored factors (and to start two engines identically). */
+isvd_status isvd_create_from_factors(const isvd_config* cfg, const void* A0, int64_t m0, int64_t n0,
+                                     int64_t lda, const void* U0, const double* sigma0,
+                                     const void* V0, int r0, int k, int on_device, isvd_t* out);
+
+/* Row append, Section 2.2 / Algorithm A1: A <- [A; x^T], then the projection
+ * p = x^T V, residual rho = ||x^T - p V^T||, the (r+1)x(r+1) core SVD and the rotations
+ * U' = blkdiag(U, 1) U_K, V' = [V z_hat] V_K, truncated to k. x has n elements. */
+isvd_status isvd_append_row(isvd_t h, const void* x, int64_t n, int on_device);
+
+/* Column append via transpose, Section 2.2 / Algorithm A2: A <- [A, y]; y has m elements. */
+isvd_status isvd_append_col(isvd_t h, const void* y, int64_t m, int on_device);
+
+/* Rank-1 entry update, Section 2.3 / Algorithm A3: A_ij <- A_ij + delta and
+ * U'S'V'^T = P_U (A_hat + delta e_i e_j^T) P_V at fixed rank, Eq. (rank1-projection). */
+isvd_status isvd_update_entry(isvd_t h, int64_t i, int64_t j, double delta);
+
+/* Applies nev events in order (same semantics as the three calls above, policy included).
+ * payload holds the row/column vectors, host or device memory. */
+isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload,
+                              int64_t payload_len, int payload_on_device);
+
+/* Sets the policy evaluated after every update (Section 3). NULL disables it. */
+isvd_status isvd_set_policy(isvd_t h, const isvd_policy* pol);
+
+/* Refresh, Section 2.4: (U, S, V) <- TruncatedSVD(A_t, k_t); U_ref <- U_t if
+ * store_initial_subspace. */
+isvd_status isvd_refresh(isvd_t h, int store_initial_subspace);
+
+/* Metrics of Section 2.5 on the current state (synchronises). */
+isvd_status isvd_metrics(isvd_t h, int flags, isvd_metrics_t* out);
+
+/* Metrics computed at the most recent policy check step (before any refresh that the check
+ * triggered; t_last == t tells that one fired). Zeroed until the first check. */
+isvd_status isvd_last_check_metrics(isvd_t h, isvd_metrics_t* out);
+
+/* Copies U (m x r), sigma (r) and V (n x r) into caller buffers (any may be NULL). */
+isvd_status isvd_get_factors(isvd_t h, void* U, double* sigma, void* V, int to_device);
+
+/* Copies the stored dense A_t (m x n, row stride n) into a caller buffer. */
+isvd_status isvd_get_matrix(isvd_t h, void* A, int to_device);
+
+/* Current shape and ranks (synchronises, so r is the device's value). */
+isvd_status isvd_get_shape(isvd_t h, int64_t* m, int64_t* n, int32_t* r, int32_t* k);
+
+/* Runs the loss-of-orthogonality monitor now and, if max|Q^T Q - I| exceeds the configured
+ * tolerance for U or V, re-orthonormalises both by two Cholesky-QR passes (sigma unchanged). */
+isvd_status isvd_reorthogonalize(isvd_t h, int force, double* err_u, double* err_v);
+
+/* Waits for all queued work; reports sticky device-side errors. */
+isvd_status isvd_sync(isvd_t h);
+
+/* Number of kernels this handle has launched so far. */
+int64_t isvd_kernel_launches(isvd_t h);
+
+/* Kernel classes for isvd_profile_read. */
+#define ISVD_KCLASS_PROJ 0     /* projection and residual passes (Eq. row-residual) */
+#define ISVD_KCLASS_CORE 1     /* core SVD (assembly, Jacobi, sort, truncation) */
+#define ISVD_KCLASS_ROTATE 2   /* rotations of U and V */
+#define ISVD_KCLASS_CHECK 3    /* policy checks: metrics incl. the truncated SVD of A */
+#define ISVD_KCLASS_REFRESH 4  /* refreshes */
+#define ISVD_KCLASS_REORTH 5   /* orthogonality monitor and re-orthogonalisation */
+#define ISVD_NUM_KCLASS 6
+
+/* Enables (1) or disables (0) device-time profiling and clears its counters. While enabled,
+ * CUDA events are recorded around every launch of the classes above and at the end of every
+ * update, on the handle's stream. */
+isvd_status isvd_profile(isvd_t h, int enable);
+
+/* Totals since isvd_profile: device milliseconds, algorithmic bytes (the bytes the method must
+ * move, e.g. U and V read and written once for a rotation) and launches of one class. */
+isvd_status isvd_profile_read(isvd_t h, int cls, double* total_ms, double* bytes, int64_t* launches);
+
+/* Device time of each update since isvd_profile (microseconds between consecutive update ends
+ * on the stream), up to cap values; *count receives the total number. */
+isvd_status isvd_latencies(isvd_t h, double* us, int64_t cap, int64_t* count);
+
+const char* isvd_last_error(isvd_t h);
+const char* isvd_status_string(isvd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISVD_H_ */

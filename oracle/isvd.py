@@ -146,8 +146,8 @@ class Policy:
 
     Reading (evaluation time): the policy runs after every update (t counts all
     three update kinds, Section 3.1); error, angle and EVR signals are recomputed
-    only on check steps (t % check_every == 0), which is where the full SVD of A_t is
-    taken (Section 4: "at each logged step we compute a full SVD").
+    only on check steps (t % check_every == 0), the steps at which Section 4 takes a full
+    SVD of A_t.
     """
 
     kind: int = POLICY_NONE
@@ -216,18 +216,21 @@ class _Dense:
 class OracleISVD:
     """State (U, sigma, V, A, N_t, t, U_ref) and the three update rules.
 
-    ``create`` follows Algorithm 1 lines 1-2 and Section 2.4: (U, S, V) from the
+    ``create`` follows the initialisation of Algorithm 1 and Section 2.4: (U, S, V) from the
     truncated SVD of A0 at rank r0 = min(k, m0, n0) (Reading: the paper's rank-k
     truncated SVD when A0 has fewer than k rows or columns), N_0 = ||A0||_F^2,
     U_ref = U_0.
     """
 
-    def __init__(self, A0, k, tol_rel=1e-10, policy: Policy | None = None):
+    def __init__(self, A0, k, tol_rel=1e-10, policy: Policy | None = None, factors=None):
         self.A = _Dense(A0)
         self.k = int(k)          # current working rank k_t
         self.tol_rel = float(tol_rel)
         self.policy = policy or Policy()
-        self.U, self.s, self.V = truncated_svd(self.A.view(), self.k)
+        if factors is None:
+            self.U, self.s, self.V = truncated_svd(self.A.view(), self.k)
+        else:                    # resume from given factors (U0, sigma0, V0)
+            self.U, self.s, self.V = (np.array(f, dtype=np.float64, copy=True) for f in factors)
         self.N = float(np.sum(self.A.view() ** 2))   # N_0 = ||A_0||_F^2
         self.U_ref = self.U.copy()
         self.t = 0

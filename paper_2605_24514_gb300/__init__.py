@@ -1,0 +1,290 @@
+"""GB300 (sm_103a) engine for the Brand-style incremental SVD of arXiv 2605.24514.
+
+This module is a thin ``ctypes`` binding of ``libisvd.so`` (C ABI in ``include/isvd.h``): it only
+marshals arguments. Every step of the update, refresh and metrics paths runs in the library's
+CUDA kernels; there is no CPU fallback, and using the engine without the built library raises.
+
+Host inputs are NumPy arrays; device inputs are CUDA tensors (``torch``), passed by pointer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libisvd.so")
+
+FP64, FP32 = 0, 1
+ROW, COL, ENTRY = 0, 1, 2
+POLICY_NONE, POLICY_PERIODIC, POLICY_ERROR, POLICY_ANGLE, POLICY_ADAPTIVE_RANK = 0, 1, 2, 4, 8
+METRICS_CHEAP, METRICS_FULL = 0, 1
+KCLASS = {"proj": 0, "core": 1, "rotate": 2, "check": 3, "refresh": 4, "reorth": 5}
+
+STATUS = {0: "ok", 1: "EINVAL", 2: "ESHAPE", 3: "EBOUNDS", 4: "ENOMEM", 5: "EBUDGET",
+          6: "ENOTCONV", 7: "ETIMEOUT", 8: "ECUDA", 9: "ENONFINITE"}
+
+
+class IsvdError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Config(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("k_max", C.c_int32), ("tol_rel", C.c_double),
+                ("row_cap", C.c_int64), ("col_cap", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("seed", C.c_uint64), ("orth_tol", C.c_double), ("orth_every", C.c_int64),
+                ("rsvd_oversample", C.c_int32), ("rsvd_power_iters", C.c_int32)]
+
+
+class Policy(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("k_min", C.c_int32), ("k_max", C.c_int32),
+                ("store_initial_subspace", C.c_int32), ("T_refresh", C.c_int64), ("T_min", C.c_int64),
+                ("check_every", C.c_int64), ("gamma", C.c_double), ("theta_max_rad", C.c_double),
+                ("tau_evr", C.c_double)]
+
+
+class Metrics(C.Structure):
+    _fields_ = [("t", C.c_int64), ("m", C.c_int64), ("n", C.c_int64), ("r", C.c_int32), ("k", C.c_int32),
+                ("frob_error", C.c_double), ("frob_opt", C.c_double), ("frob_gap", C.c_double),
+                ("frob_ratio", C.c_double), ("angle", C.c_double), ("angle_to_opt", C.c_double),
+                ("evr", C.c_double), ("rho_last", C.c_double), ("novelty_last", C.c_double),
+                ("orth_err_u", C.c_double), ("orth_err_v", C.c_double), ("N", C.c_double),
+                ("refreshes", C.c_int64), ("reorths", C.c_int64), ("t_last", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Event(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("i", C.c_int64), ("j", C.c_int64),
+                ("delta", C.c_double), ("off", C.c_int64), ("len", C.c_int64)]
+
+
+_lib = None
+
+_SIGS = {
+    "isvd_create": (C.c_int, [C.POINTER(Config), C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                              C.POINTER(C.c_void_p)]),
+    "isvd_create_from_factors": (C.c_int, [C.POINTER(Config), C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                           C.POINTER(C.c_void_p)]),
+    "isvd_destroy": (None, [C.c_void_p]),
+    "isvd_append_row": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "isvd_append_col": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "isvd_update_entry": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double]),
+    "isvd_apply_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int]),
+    "isvd_set_policy": (C.c_int, [C.c_void_p, C.POINTER(Policy)]),
+    "isvd_refresh": (C.c_int, [C.c_void_p, C.c_int]),
+    "isvd_metrics": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Metrics)]),
+    "isvd_last_check_metrics": (C.c_int, [C.c_void_p, C.POINTER(Metrics)]),
+    "isvd_get_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "isvd_get_matrix": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "isvd_get_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32)]),
+    "isvd_reorthogonalize": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "isvd_sync": (C.c_int, [C.c_void_p]),
+    "isvd_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "isvd_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "isvd_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64)]),
+    "isvd_latencies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "isvd_last_error": (C.c_char_p, [C.c_void_p]),
+    "isvd_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    """Loads ``libisvd.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2605_24514_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, on_device) for a NumPy array or a CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_cuda:
+            return a.data_ptr(), 0
+        return a.data_ptr(), 1
+    raise TypeError(type(a))
+
+
+class ISVD:
+    """One incremental-SVD stream (a ``libisvd`` handle)."""
+
+    def __init__(self, A0, k, prec=FP64, k_max=0, tol_rel=0.0, stream=None, row_cap=0, col_cap=0,
+                 seed=0, orth_tol=0.0, orth_every=0, rsvd_oversample=0, rsvd_power_iters=-1, factors=None):
+        """``factors`` = (U0, sigma0, V0) host arrays to start from instead of computing the
+        truncated SVD of A0 (isvd_create_from_factors)."""
+        self.prec = prec
+        self.dtype = np.float64 if prec == FP64 else np.float32
+        if isinstance(A0, np.ndarray):
+            A0 = np.ascontiguousarray(A0, dtype=self.dtype)
+        m0, n0 = A0.shape
+        cfg = Config(prec=prec, k_max=k_max, tol_rel=tol_rel, row_cap=row_cap, col_cap=col_cap,
+                     cuda_stream=stream or 0, seed=seed, orth_tol=orth_tol, orth_every=orth_every,
+                     rsvd_oversample=rsvd_oversample, rsvd_power_iters=rsvd_power_iters)
+        ptr, dev = _ptr(A0)
+        h = C.c_void_p()
+        self._h = None
+        if factors is None:
+            st = lib().isvd_create(C.byref(cfg), ptr, m0, n0, n0, int(k), dev, C.byref(h))
+        else:
+            U0, s0, V0 = factors
+            U0 = np.ascontiguousarray(U0, dtype=self.dtype)
+            V0 = np.ascontiguousarray(V0, dtype=self.dtype)
+            s0 = np.ascontiguousarray(s0, dtype=np.float64)
+            st = lib().isvd_create_from_factors(C.byref(cfg), ptr, m0, n0, n0, U0.ctypes.data, s0.ctypes.data,
+                                                V0.ctypes.data, int(s0.size), int(k), dev, C.byref(h))
+        if st:
+            raise IsvdError(st, "isvd_create")
+        self._h = h
+
+    def _check(self, st, what):
+        if st:
+            raise IsvdError(st, f"{what}: {lib().isvd_last_error(self._h).decode()}")
+
+    def _vec(self, v):
+        if isinstance(v, np.ndarray):
+            v = np.ascontiguousarray(v, dtype=self.dtype)
+        return v
+
+    def append_row(self, x):
+        x = self._vec(x)
+        p, d = _ptr(x)
+        self._check(lib().isvd_append_row(self._h, p, x.shape[0], d), "append_row")
+
+    def append_col(self, y):
+        y = self._vec(y)
+        p, d = _ptr(y)
+        self._check(lib().isvd_append_col(self._h, p, y.shape[0], d), "append_col")
+
+    def update_entry(self, i, j, delta):
+        self._check(lib().isvd_update_entry(self._h, int(i), int(j), float(delta)), "update_entry")
+
+    def apply_events(self, events, payload=None):
+        """Applies a ``streams.EventStream`` (payload converted to the storage type) in one call.
+        ``payload`` may be given as a CUDA tensor to keep it on the device."""
+        n = len(events)
+        arr = (Event * max(n, 1))()
+        for e in range(n):
+            arr[e].kind = int(events.kind[e])
+            arr[e].i = int(events.i[e])
+            arr[e].j = int(events.j[e])
+            arr[e].delta = float(events.delta[e])
+            arr[e].off = int(events.off[e])
+            arr[e].len = int(events.length[e])
+        if payload is None:
+            payload = np.ascontiguousarray(events.payload, dtype=self.dtype)
+        p, d = _ptr(payload)
+        plen = payload.shape[0] if len(payload.shape) else 0
+        self._check(lib().isvd_apply_events(self._h, arr, n, p, plen, d), "apply_events")
+
+    def set_policy(self, kind=POLICY_NONE, T_refresh=0, T_min=0, check_every=0, gamma=1.1,
+                   theta_max=np.pi / 2, tau_evr=0.9, k_min=1, k_max=0, store_initial_subspace=False):
+        pol = Policy(kind=kind, k_min=k_min, k_max=k_max, store_initial_subspace=int(store_initial_subspace),
+                     T_refresh=T_refresh, T_min=T_min, check_every=check_every, gamma=gamma,
+                     theta_max_rad=theta_max, tau_evr=tau_evr)
+        self._check(lib().isvd_set_policy(self._h, C.byref(pol)), "set_policy")
+
+    def refresh(self, store_initial_subspace=False):
+        self._check(lib().isvd_refresh(self._h, int(store_initial_subspace)), "refresh")
+
+    def metrics(self, full=True):
+        mt = Metrics()
+        self._check(lib().isvd_metrics(self._h, METRICS_FULL if full else METRICS_CHEAP, C.byref(mt)), "metrics")
+        return mt.as_dict()
+
+    def last_check_metrics(self):
+        mt = Metrics()
+        self._check(lib().isvd_last_check_metrics(self._h, C.byref(mt)), "last_check_metrics")
+        return mt.as_dict()
+
+    def shape(self):
+        m, n, r, k = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        self._check(lib().isvd_get_shape(self._h, C.byref(m), C.byref(n), C.byref(r), C.byref(k)), "get_shape")
+        return m.value, n.value, r.value, k.value
+
+    def factors(self):
+        m, n, r, _ = self.shape()
+        U = np.empty((m, r), self.dtype)
+        V = np.empty((n, r), self.dtype)
+        s = np.empty(r, np.float64)
+        self._check(lib().isvd_get_factors(self._h, U.ctypes.data, s.ctypes.data, V.ctypes.data, 0), "get_factors")
+        return U, s, V
+
+    def sigma(self):
+        """Current singular values (device to host copy of r doubles)."""
+        r = self.shape()[2]
+        s = np.empty(r, np.float64)
+        self._check(lib().isvd_get_factors(self._h, None, s.ctypes.data, None, 0), "get_factors")
+        return s
+
+    def matrix(self):
+        m, n, _, _ = self.shape()
+        A = np.empty((m, n), self.dtype)
+        self._check(lib().isvd_get_matrix(self._h, A.ctypes.data, 0), "get_matrix")
+        return A
+
+    def reorthogonalize(self, force=False):
+        eu, ev = C.c_double(), C.c_double()
+        self._check(lib().isvd_reorthogonalize(self._h, int(force), C.byref(eu), C.byref(ev)), "reorthogonalize")
+        return eu.value, ev.value
+
+    def sync(self):
+        self._check(lib().isvd_sync(self._h), "sync")
+
+    @property
+    def launches(self):
+        return int(lib().isvd_kernel_launches(self._h))
+
+    def profile(self, enable=True):
+        """Starts (or stops) CUDA-event timing of each kernel class and of each update."""
+        self._check(lib().isvd_profile(self._h, int(enable)), "profile")
+
+    def profile_read(self):
+        """{class: (device ms, algorithmic bytes, launches)} since ``profile()``."""
+        out = {}
+        for name, c in KCLASS.items():
+            ms, by, n = C.c_double(), C.c_double(), C.c_int64()
+            self._check(lib().isvd_profile_read(self._h, c, C.byref(ms), C.byref(by), C.byref(n)), "profile_read")
+            out[name] = (ms.value, by.value, n.value)
+        return out
+
+    def latencies_us(self):
+        n = C.c_int64()
+        self._check(lib().isvd_latencies(self._h, None, 0, C.byref(n)), "latencies")
+        buf = np.empty(max(n.value, 1), np.float64)
+        self._check(lib().isvd_latencies(self._h, buf.ctypes.data, buf.size, C.byref(n)), "latencies")
+        return buf[:n.value]
+
+    def close(self):
+        if self._h:
+            lib().isvd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

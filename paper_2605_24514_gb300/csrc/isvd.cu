@@ -1,0 +1,1213 @@
+// libisvd host side: the C ABI declared in include/isvd.h.
+//
+// One handle = one stream of updates on one GPU. Device state (U, V, A, sigma, N_t, rank) is
+// resident in HBM and only kernels touch it, so consecutive updates queue back to back on the
+// handle's CUDA stream with no host round trip; the host synchronises only for metrics, policy
+// checks and explicit reads.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/isvd.h"
+#include "refresh_kernels.cuh"
+#include "update_kernels.cuh"
+
+using namespace isvd;
+
+struct isvd_ctx {
+  int prec = ISVD_FP64;
+  size_t es = 8;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int64_t m = 0, n = 0, row_cap = 0, col_cap = 0;
+  int kmax = 0, ld = 0, k_host = 0;
+  double tol_rel = 1e-10, orth_tol = 1e-12;
+  int64_t orth_every = 0, since_orth = 0;
+  void* U = nullptr;
+  void* V = nullptr;
+  void* A = nullptr;
+  void* Uref = nullptr;
+  int64_t m_ref = 0, uref_cap = 0;
+  int r_ref = 0;
+  DevState* st = nullptr;
+  double* sig = nullptr;
+  double* p = nullptr;
+  double* part = nullptr;
+  void* UK = nullptr;
+  void* VK = nullptr;
+  void* xbuf = nullptr;
+  int64_t xbuf_cap = 0;
+  // refresh / metrics workspace
+  double* G = nullptr;
+  int64_t G_cap = 0;
+  double* small = nullptr;  // several (kKmaxLimit+1)^2 FP64 scratch matrices
+  double* evals = nullptr;
+  double* inv = nullptr;
+  double* scal = nullptr;  // scalars: [0] E_inc^2, [1] tail, [2] max offident, ...
+  int* info = nullptr;
+  void* Rtmp = nullptr;
+  void* Uopt = nullptr;
+  int64_t uopt_cap = 0;
+  void* Vopt = nullptr;
+  int64_t vopt_cap = 0;
+  double* sig_opt = nullptr;
+  double* Cbuf = nullptr;
+  int64_t cbuf_cap = 0;
+  // randomized refresh workspace
+  void* Yb = nullptr;
+  int64_t yb_cap = 0;
+  void* Om = nullptr;
+  int64_t om_cap = 0;
+  double* Zd = nullptr;
+  int64_t zd_cap = 0;
+  void* Rl = nullptr;
+  int64_t rl_cap = 0;
+  int rsvd_p = 16, rsvd_q = 2;
+  uint64_t seed = 0;
+  int64_t rsvd_calls = 0;
+  isvd_policy pol{};
+  int has_pol = 0;
+  int64_t t = 0, t_last = 0, refreshes = 0, reorths = 0, launches = 0;
+  double orth_err_u = 0, orth_err_v = 0;
+  isvd_metrics_t last_check{};
+  int sticky = ISVD_OK;
+  std::string err;
+  // profiling (events around launches; per-update stamps)
+  int prof = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Span {
+    int cls;
+    size_t a, b;
+    double bytes;
+  };
+  std::vector<Span> spans;
+  std::vector<size_t> stamps;  // event index at the end of each update
+  int cur_cls = -1;
+  size_t cur_a = 0;
+  double cur_bytes = 0;
+  double cls_ms[ISVD_NUM_KCLASS] = {0};
+  double cls_bytes[ISVD_NUM_KCLASS] = {0};
+  int64_t cls_n[ISVD_NUM_KCLASS] = {0};
+  std::vector<double> lat_us;
+};
+
+namespace {
+
+constexpr int kSmall = (kKmaxLimit + 1) * (kKmaxLimit + 1);
+
+// ---- profiling helpers ----------------------------------------------------------------------
+
+size_t prof_event(isvd_ctx* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  cudaEventRecord(h->ev_pool[h->ev_used], h->stream);
+  return h->ev_used++;
+}
+
+// Marks the start of a launch of kernel class cls moving `bytes` algorithmic bytes.
+void prof_begin(isvd_ctx* h, int cls, double bytes) {
+  if (!h->prof) return;
+  h->cur_cls = cls;
+  h->cur_a = prof_event(h);
+  h->cur_bytes = bytes;
+}
+
+void prof_end(isvd_ctx* h) {
+  if (!h->prof || h->cur_cls < 0) return;
+  const size_t b = prof_event(h);
+  h->spans.push_back({h->cur_cls, h->cur_a, b, h->cur_bytes});
+  h->cur_cls = -1;
+}
+
+void prof_stamp(isvd_ctx* h) {
+  if (!h->prof) return;
+  h->stamps.push_back(prof_event(h));
+}
+
+// Resolves recorded events into per-class totals and per-update latencies (synchronises).
+void prof_flush(isvd_ctx* h) {
+  if (h->ev_used == 0) return;
+  cudaEventSynchronize(h->ev_pool[h->ev_used - 1]);
+  for (const auto& sp : h->spans) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev_pool[sp.a], h->ev_pool[sp.b]);
+    h->cls_ms[sp.cls] += ms;
+    h->cls_bytes[sp.cls] += sp.bytes;
+    h->cls_n[sp.cls] += 1;
+  }
+  for (size_t i = 1; i < h->stamps.size(); ++i) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev_pool[h->stamps[i - 1]], h->ev_pool[h->stamps[i]]);
+    h->lat_us.push_back(ms * 1e3);
+  }
+  size_t keep = h->stamps.empty() ? 0 : h->stamps.back();
+  h->spans.clear();
+  if (!h->stamps.empty()) {
+    // keep the last stamp as the origin of the next update's latency
+    std::swap(h->ev_pool[0], h->ev_pool[keep]);
+    h->stamps.assign(1, 0);
+    h->ev_used = 1;
+  } else {
+    h->ev_used = 0;
+  }
+}
+
+isvd_status fail(isvd_ctx* h, isvd_status s, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (s == ISVD_ECUDA || s == ISVD_ENOTCONV || s == ISVD_ENONFINITE || s == ISVD_ETIMEOUT) h->sticky = s;
+  }
+  return s;
+}
+
+#define CK(h, x)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      return fail((h), ISVD_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+#define CKL(h)                                                                            \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      return fail((h), ISVD_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    (h)->launches++;                                                                      \
+  } while (0)
+
+int kb_bucket(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int core_threads(int kmax) {
+  const int nc = kmax + 1;
+  const int npairs = (nc + 1) / 2;
+  int warps = (npairs + 1) / 2;
+  warps = std::max(2, std::min(32, warps));
+  return warps * 32;
+}
+
+template <typename T>
+bool host_finite(const T* v, int64_t len) {
+  for (int64_t i = 0; i < len; ++i)
+    if (!std::isfinite((double)v[i])) return false;
+  return true;
+}
+
+template <typename T, int KB>
+isvd_status set_rot_attr(isvd_ctx* h) {
+  CK(h, cudaFuncSetAttribute(k_rotate<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<T, KB>()));
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status set_attrs(isvd_ctx* h) {
+  isvd_status s;
+  if ((s = set_rot_attr<T, 16>(h)) || (s = set_rot_attr<T, 32>(h)) || (s = set_rot_attr<T, 64>(h)) ||
+      (s = set_rot_attr<T, 128>(h)))
+    return s;
+  using JT = T;
+  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<JT>(h->kmax);
+  CK(h, cudaFuncSetAttribute(k_core<T, JT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  CK(h, cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+  CK(h, cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+  CK(h, cudaFuncSetAttribute(k_chol_rinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((kKmaxLimit + 1) * (kKmaxLimit + 1) * sizeof(double))));
+  CK(h, cudaFuncSetAttribute(k_resid_norm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kKmaxLimit * (kResTile + 1) * sizeof(T))));
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status launch_rotate(isvd_ctx* h, const RotSide& s0, const RotSide& s1, int kb, const T* xz, const double* p) {
+  // Side 0 always gets at least one block (its new row may be the only work).
+  const int64_t t0e = std::max<int64_t>(1, (s0.rows + kRotRows - 1) / kRotRows);
+  const int64_t t1 = s1.rows > 0 ? (s1.rows + kRotRows - 1) / kRotRows : 0;
+  const int64_t tiles = t0e + t1;
+  switch (kb) {
+    case 16:
+      k_rotate<T, 16><<<(unsigned)tiles, kRotThreads, rot_smem_bytes<T, 16>(), h->stream>>>(s0, s1, (int)t0e, xz, p, h->st);
+      break;
+    case 32:
+      k_rotate<T, 32><<<(unsigned)tiles, kRotThreads, rot_smem_bytes<T, 32>(), h->stream>>>(s0, s1, (int)t0e, xz, p, h->st);
+      break;
+    case 64:
+      k_rotate<T, 64><<<(unsigned)tiles, kRotThreads, rot_smem_bytes<T, 64>(), h->stream>>>(s0, s1, (int)t0e, xz, p, h->st);
+      break;
+    default:
+      k_rotate<T, 128><<<(unsigned)tiles, kRotThreads, rot_smem_bytes<T, 128>(), h->stream>>>(s0, s1, (int)t0e, xz, p, h->st);
+      break;
+  }
+  CKL(h);
+  return ISVD_OK;
+}
+
+// ---- memory ------------------------------------------------------------------------------
+
+isvd_status dmalloc(isvd_ctx* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, ISVD_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return ISVD_OK;
+}
+
+isvd_status ensure_rows(isvd_ctx* h, int64_t need) {
+  if (need <= h->row_cap) return ISVD_OK;
+  const int64_t cap = std::max(need, h->row_cap * 2);
+  void *U2 = nullptr, *A2 = nullptr;
+  isvd_status s;
+  if ((s = dmalloc(h, &U2, (size_t)cap * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, &A2, (size_t)cap * h->col_cap * h->es))) {
+    cudaFree(U2);
+    return s;
+  }
+  CK(h, cudaMemcpyAsync(U2, h->U, (size_t)h->m * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(A2, h->A, (size_t)h->m * h->col_cap * h->es, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  cudaFree(h->U);
+  cudaFree(h->A);
+  h->U = U2;
+  h->A = A2;
+  h->row_cap = cap;
+  return ISVD_OK;
+}
+
+isvd_status ensure_cols(isvd_ctx* h, int64_t need) {
+  if (need <= h->col_cap) return ISVD_OK;
+  const int64_t cap = std::max(need, h->col_cap * 2);
+  void *V2 = nullptr, *A2 = nullptr;
+  isvd_status s;
+  if ((s = dmalloc(h, &V2, (size_t)cap * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, &A2, (size_t)h->row_cap * cap * h->es))) {
+    cudaFree(V2);
+    return s;
+  }
+  CK(h, cudaMemcpyAsync(V2, h->V, (size_t)h->n * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpy2DAsync(A2, cap * h->es, h->A, h->col_cap * h->es, h->n * h->es, h->m, cudaMemcpyDeviceToDevice,
+                          h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  cudaFree(h->V);
+  cudaFree(h->A);
+  h->V = V2;
+  h->A = A2;
+  h->col_cap = cap;
+  return ISVD_OK;
+}
+
+isvd_status ensure_buf(isvd_ctx* h, void** buf, int64_t* cap, int64_t need_bytes) {
+  if (need_bytes <= *cap) return ISVD_OK;
+  if (*buf) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(*buf);
+    *buf = nullptr;
+  }
+  const int64_t c = std::max(need_bytes, *cap * 2);
+  isvd_status s = dmalloc(h, buf, (size_t)c);
+  if (s) {
+    *cap = 0;
+    return s;
+  }
+  *cap = c;
+  return ISVD_OK;
+}
+
+// ---- single update ------------------------------------------------------------------------
+
+int proj_blocks(int64_t rows) {
+  int64_t b = (rows + 63) / 64;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxProjBlocks));
+}
+
+// Row append (kind kRow, x over the n columns) or column append (kind kCol, x over the m rows),
+// x already on the device. Section 2.2 Steps 1-3 / Algorithms A1, A2.
+template <typename T>
+isvd_status do_append(isvd_ctx* h, int kind, const T* x) {
+  isvd_status s;
+  if (kind == kRow) {
+    if ((s = ensure_rows(h, h->m + 1))) return s;
+  } else {
+    if ((s = ensure_cols(h, h->n + 1))) return s;
+  }
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  T* A = (T*)h->A;
+  const int64_t lda = h->col_cap;
+  // Projection side X: V for a row append (x over columns), U for a column append.
+  const T* X = kind == kRow ? V : U;
+  const int64_t rows = kind == kRow ? h->n : h->m;
+  T* dst = kind == kRow ? A + h->m * lda : A + h->n;
+  const int64_t dst_stride = kind == kRow ? 1 : lda;
+  const int nb = proj_blocks(rows);
+  const double kk = (double)h->k_host;
+  prof_begin(h, ISVD_KCLASS_PROJ, (double)rows * (kk + 2) * h->es);  // X, x read; x written into A
+  k_proj1<T><<<nb, kProjThreads, 0, h->stream>>>(X, h->ld, rows, x, h->st, h->part, h->p, dst, dst_stride);
+  CKL(h);
+  prof_end(h);
+  prof_begin(h, ISVD_KCLASS_PROJ, (double)rows * (kk + 1) * h->es);  // X, x read
+  if (sizeof(T) == sizeof(float)) {
+    k_proj2<T, true><<<nb, kProjThreads, 0, h->stream>>>(X, h->ld, rows, x, h->st, h->part, h->p, h->tol_rel);
+  } else {
+    k_proj2<T, false><<<nb, kProjThreads, 0, h->stream>>>(X, h->ld, rows, x, h->st, h->part, h->p, h->tol_rel);
+  }
+  CKL(h);
+  prof_end(h);
+  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<T>(h->kmax);
+  prof_begin(h, ISVD_KCLASS_CORE, 2.0 * (kk + 1) * kk * h->es);
+  k_core<T, T><<<1, core_threads(h->kmax), cs, h->stream>>>(kind, h->st, h->sig, h->p, U, V, h->ld, 0, 0, 0.0, A, lda,
+                                                            (T*)h->UK, (T*)h->VK, h->ld);
+  CKL(h);
+  prof_end(h);
+  // Rotations. Row append: U side uses U_K plus the new row, V side uses V_K plus z_hat.
+  // Column append (transpose): U side uses V_K plus z_hat, V side uses U_K plus the new row.
+  RotSide su{}, sv{};
+  su.X = su.Y = U;
+  su.rows = h->m;
+  su.ldx = su.ldy = h->ld;
+  su.ldr = h->ld;
+  su.c_in = -1;
+  su.k_out = -1;
+  sv = su;
+  sv.X = sv.Y = V;
+  sv.rows = h->n;
+  if (kind == kRow) {
+    su.R = h->UK;
+    su.newrow = 1;
+    sv.R = h->VK;
+    sv.zhat = 1;
+  } else {
+    su.R = h->VK;
+    su.zhat = 1;
+    sv.R = h->UK;
+    sv.newrow = 1;
+  }
+  // U and V read and written once, plus the z_hat source vector.
+  prof_begin(h, ISVD_KCLASS_ROTATE, (2.0 * (h->m + h->n) * kk + (double)rows) * h->es);
+  if ((s = launch_rotate<T>(h, su, sv, kb_bucket(h->kmax), x, h->p))) return s;
+  prof_end(h);
+  if (kind == kRow) h->m += 1;
+  else h->n += 1;
+  return ISVD_OK;
+}
+
+// Rank-1 entry update, Section 2.3 / Algorithm A3.
+template <typename T>
+isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  const double kk = (double)h->k_host;
+  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<T>(h->kmax);
+  prof_begin(h, ISVD_KCLASS_CORE, 2.0 * kk * kk * h->es);
+  k_core<T, T><<<1, core_threads(h->kmax), cs, h->stream>>>(kEntry, h->st, h->sig, h->p, U, V, h->ld, i, j, delta,
+                                                            (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld);
+  CKL(h);
+  prof_end(h);
+  RotSide su{}, sv{};
+  su.X = su.Y = U;
+  su.rows = h->m;
+  su.ldx = su.ldy = h->ld;
+  su.ldr = h->ld;
+  su.c_in = -1;
+  su.k_out = -1;
+  su.R = h->UK;
+  sv = su;
+  sv.X = sv.Y = V;
+  sv.rows = h->n;
+  sv.R = h->VK;
+  prof_begin(h, ISVD_KCLASS_ROTATE, 2.0 * (h->m + h->n) * kk * h->es);
+  isvd_status s = launch_rotate<T>(h, su, sv, kb_bucket(h->kmax), (const T*)nullptr, h->p);
+  prof_end(h);
+  return s;
+}
+
+// ---- truncated SVD of A (refresh and metrics) ----------------------------------------------
+
+// C (rc x cc, FP64) = X^T Y over `rows` rows.
+template <typename T>
+isvd_status gemm_tn(isvd_ctx* h, const T* X, int64_t ldx, int cx, const T* Y, int64_t ldy, int cy, int64_t rows,
+                    double* C) {
+  CK(h, cudaMemsetAsync(C, 0, (size_t)cx * cy * 8, h->stream));
+  if (rows <= 0) return ISVD_OK;
+  const int64_t splits_target = 304;
+  int64_t rps = (rows + splits_target - 1) / splits_target;
+  rps = std::max<int64_t>(kTnChunk, (rps + kTnChunk - 1) / kTnChunk * kTnChunk);
+  dim3 grid((unsigned)((cx + kTnTile - 1) / kTnTile), (unsigned)((cy + kTnTile - 1) / kTnTile),
+            (unsigned)((rows + rps - 1) / rps));
+  k_gemm_tn<T><<<grid, 256, 0, h->stream>>>(X, ldx, cx, Y, ldy, cy, rows, rps, C, cy);
+  CKL(h);
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status sym_eig(isvd_ctx* h, const double* G, int n, double* evals, double* evecs, int fp64) {
+  const int threads = core_threads(std::max(n - 1, 1));
+  if (fp64 && n <= 80) {
+    const size_t sm = (size_t)2 * n * n * sizeof(double) + (size_t)n * 12 + 64;
+    k_sym_eig<double><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info);
+  } else {
+    const size_t sm = (size_t)2 * n * n * sizeof(float) + (size_t)n * 12 + 64;
+    k_sym_eig<float><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info);
+  }
+  CKL(h);
+  return ISVD_OK;
+}
+
+
+isvd_status sticky_check(isvd_ctx* h) {
+  if (h->sticky) return (isvd_status)h->sticky;
+  return ISVD_OK;
+}
+
+isvd_status read_state(isvd_ctx* h, DevState* out) {
+  CK(h, cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (out->status & kStNonFinite) return fail(h, ISVD_ENONFINITE, "non-finite value in a device input");
+  if (out->status & kStNotConv) return fail(h, ISVD_ENOTCONV, "core Jacobi SVD did not converge");
+  if (out->status & kStTimeout) return fail(h, ISVD_ETIMEOUT, "device wait timed out");
+  return ISVD_OK;
+}
+
+// In-place orthonormalisation of the columns of Q (rows x l, row stride l) by Cholesky-QR: a
+// first pass with a small diagonal shift (robust when Q is rank deficient), then two plain
+// passes (Fukaya et al.'s shifted CholeskyQR3).
+template <typename T>
+isvd_status orth_cols(isvd_ctx* h, T* Q, int64_t rows, int l) {
+  isvd_status s;
+  double* B = h->small + 4 * kSmall;
+  for (int pass = 0; pass < 3; ++pass) {
+    if ((s = gemm_tn<T>(h, Q, l, l, Q, l, l, rows, B))) return s;
+    if (pass == 0) {
+      k_add_diag<<<1, 128, 0, h->stream>>>(B, l, sizeof(T) == 8 ? 1e-13 : 1e-5);
+      CKL(h);
+    }
+    k_chol_rinv<T><<<1, 128, (size_t)l * l * sizeof(double), h->stream>>>(B, l, h->small + 5 * kSmall, (T*)h->Rl, l,
+                                                                          h->info);
+    CKL(h);
+    RotSide sq{};
+    sq.X = sq.Y = Q;
+    sq.rows = rows;
+    sq.ldx = sq.ldy = l;
+    sq.R = h->Rl;
+    sq.ldr = l;
+    sq.c_in = l;
+    sq.k_out = l;
+    RotSide none{};
+    if ((s = launch_rotate<T>(h, sq, none, kb_bucket(l), (const T*)nullptr, nullptr))) return s;
+  }
+  return ISVD_OK;
+}
+
+// Randomized truncated SVD of A (Halko, Martinsson and Tropp 2011) at rank kr: l = kr + p
+// columns (capped at 128 and min(m, n)), test matrix warm-started with the current V (the
+// maintained right subspace) and completed with Gaussian columns, q power iterations with
+// re-orthonormalisation between passes, then the small SVD of B = Q^T A through the Gram
+// B B^T = Z^T Z (Z = A^T Q). E_opt^2 = N_t - sum sigma^2.
+template <typename T>
+isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm) {
+  const int64_t m = h->m, n = h->n, lda = h->col_cap;
+  const T* A = (const T*)h->A;
+  isvd_status s;
+  const int l = (int)std::min<int64_t>(std::min<int64_t>(kr + h->rsvd_p, kKmaxLimit), std::min(m, n));
+  if (l < kr) return fail(h, ISVD_EINVAL, "randomized refresh: rank exceeds the sketch size");
+  if ((s = ensure_buf(h, &h->Yb, &h->yb_cap, m * l * (int64_t)h->es))) return s;
+  if ((s = ensure_buf(h, &h->Om, &h->om_cap, n * l * (int64_t)h->es))) return s;
+  if ((s = ensure_buf(h, (void**)&h->Zd, &h->zd_cap, n * l * 8))) return s;
+  if ((s = ensure_buf(h, &h->Rl, &h->rl_cap, (int64_t)l * l * (int64_t)h->es * 2))) return s;
+  T* Y = (T*)h->Yb;
+  T* Om = (T*)h->Om;
+  T* Rl2 = (T*)h->Rl + (int64_t)l * l;
+  int c0 = 0;
+  if (warm) {
+    DevState ds;
+    if ((s = read_state(h, &ds))) return s;
+    c0 = std::min(ds.r, l);
+  }
+  const uint64_t seed = h->seed * 0x9E3779B97F4A7C15ull + (uint64_t)(++h->rsvd_calls);
+  k_fill_omega<T><<<(unsigned)((n * l + 255) / 256), 256, 0, h->stream>>>(Om, n, l, l, (const T*)h->V, h->ld, c0, seed);
+  CKL(h);
+  const dim3 gy((unsigned)((m + kGemmBM - 1) / kGemmBM), (unsigned)((l + kGemmBN - 1) / kGemmBN));
+  k_gemm_nn<T><<<gy, 256, 0, h->stream>>>(A, lda, m, n, Om, l, l, Y, l);
+  CKL(h);
+  if ((s = orth_cols<T>(h, Y, m, l))) return s;
+  for (int it = 0; it <= h->rsvd_q; ++it) {
+    // Z = A^T Q (n x l, FP64)
+    if ((s = gemm_tn<T>(h, A, lda, (int)n, Y, l, l, m, h->Zd))) return s;
+    if (it == h->rsvd_q) break;
+    k_scale_cast<T><<<(unsigned)((n * l + 255) / 256), 256, 0, h->stream>>>(h->Zd, n, l, l, nullptr, Om, l);
+    CKL(h);
+    if ((s = orth_cols<T>(h, Om, n, l))) return s;
+    k_gemm_nn<T><<<gy, 256, 0, h->stream>>>(A, lda, m, n, Om, l, l, Y, l);
+    CKL(h);
+    if ((s = orth_cols<T>(h, Y, m, l))) return s;
+  }
+  double* GB = h->small + 3 * kSmall;
+  double* evecs = h->small + 2 * kSmall;
+  if ((s = gemm_tn<double>(h, h->Zd, l, l, h->Zd, l, l, n, GB))) return s;
+  if ((s = sym_eig<T>(h, GB, l, h->evals, evecs, sizeof(T) == 8))) return s;
+  k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, l, kr, sig_o, h->inv, Rl2, l, h->scal + 3);
+  CKL(h);
+  RotSide su{};
+  su.X = Y;
+  su.Y = Uo;
+  su.rows = m;
+  su.ldx = l;
+  su.ldy = h->ld;
+  su.R = Rl2;
+  su.ldr = l;
+  su.c_in = l;
+  su.k_out = kr;
+  RotSide none{};
+  if ((s = launch_rotate<T>(h, su, none, kb_bucket(l), (const T*)nullptr, nullptr))) return s;
+  k_small_gemm_cast<T><<<(unsigned)((n * kr + 255) / 256), 256, 0, h->stream>>>(h->Zd, n, l, evecs, kr, h->inv, Vo,
+                                                                                h->ld);
+  CKL(h);
+  k_tail_from_N<<<1, 32, 0, h->stream>>>(h->st, sig_o, kr, h->scal + 1);
+  CKL(h);
+  return ISVD_OK;
+}
+
+// Truncated SVD of the stored A_t at rank kr (Algorithm 1 "TruncatedSVD", Section 2.4):
+// Uo (m x kr, row stride ld), sig_o (kr), Vo (n x kr, row stride ld), and the tail energy
+// sum_{j > kr} s_j^2 in h->scal[1]. Exact path through the Gram matrix of the short side.
+template <typename T>
+isvd_status tsvd(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm = 1) {
+  const int64_t m = h->m, n = h->n;
+  const int64_t lda = h->col_cap;
+  const T* A = (const T*)h->A;
+  const int fp64 = sizeof(T) == sizeof(double);
+  if (std::min(m, n) > kKmaxLimit) return tsvd_randomized<T>(h, kr, Uo, sig_o, Vo, warm);
+  isvd_status s;
+  const int q = (int)std::min(m, n);
+  if ((s = ensure_buf(h, (void**)&h->G, &h->G_cap, (int64_t)q * q * 8 * 2))) return s;
+  double* G = h->G;
+  double* evecs = h->G + (int64_t)q * q;
+  if (n <= m) {
+    if ((s = gemm_tn<T>(h, A, lda, (int)n, A, lda, (int)n, m, G))) return s;
+    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64))) return s;
+    k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, q, kr, sig_o, h->inv, Vo, h->ld, h->scal + 1);
+    CKL(h);
+    RotSide su{};
+    su.X = A;
+    su.Y = Uo;
+    su.rows = m;
+    su.ldx = lda;
+    su.ldy = h->ld;
+    su.R = Vo;
+    su.ldr = h->ld;
+    su.c_in = (int)n;
+    su.k_out = kr;
+    su.colscale = h->inv;
+    RotSide none{};
+    none.rows = 0;
+    none.c_in = 0;
+    none.k_out = 0;
+    if ((s = launch_rotate<T>(h, su, none, kb_bucket(std::max<int>((int)n, kr)), (const T*)nullptr, nullptr))) return s;
+  } else {
+    CK(h, cudaMemsetAsync(G, 0, (size_t)q * q * 8, h->stream));
+    const int64_t e = (int64_t)m * m;
+    k_gram_rows<T><<<(unsigned)((e + 7) / 8), 256, 0, h->stream>>>(A, lda, (int)m, n, G);
+    CKL(h);
+    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64))) return s;
+    k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, q, kr, sig_o, h->inv, Uo, h->ld, h->scal + 1);
+    CKL(h);
+    // V = A^T U S^-1.
+    if ((s = ensure_buf(h, (void**)&h->Cbuf, &h->cbuf_cap, n * kr * 8))) return s;
+    CK(h, cudaMemsetAsync(h->Cbuf, 0, (size_t)n * kr * 8, h->stream));
+    const int64_t rps = std::max<int64_t>(kTnChunk, m);
+    dim3 grid((unsigned)((n + kTnTile - 1) / kTnTile), (unsigned)((kr + kTnTile - 1) / kTnTile), 1);
+    k_gemm_tn<T><<<grid, 256, 0, h->stream>>>(A, lda, (int)n, Uo, h->ld, kr, m, rps, h->Cbuf, kr);
+    CKL(h);
+    const int64_t tot = n * kr;
+    k_scale_cast<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->Cbuf, n, kr, kr, h->inv, Vo, h->ld);
+    CKL(h);
+  }
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status set_rank(isvd_ctx* h, int r) {
+  CK(h, cudaMemcpyAsync(&h->st->r, &r, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status store_ref(isvd_ctx* h, int r) {
+  isvd_status s;
+  if ((s = ensure_buf(h, &h->Uref, &h->uref_cap, h->m * h->ld * (int64_t)h->es))) return s;
+  CK(h, cudaMemcpyAsync(h->Uref, h->U, (size_t)h->m * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
+  h->m_ref = h->m;
+  h->r_ref = r;
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status do_refresh(isvd_ctx* h, int store) {
+  const int kr = (int)std::min<int64_t>(h->k_host, std::min(h->m, h->n));
+  isvd_status s;
+  if ((s = tsvd<T>(h, kr, (T*)h->U, h->sig, (T*)h->V))) return s;
+  if ((s = set_rank<T>(h, kr))) return s;
+  if (store && (s = store_ref<T>(h, kr))) return s;
+  h->t_last = h->t;
+  h->refreshes++;
+  return ISVD_OK;
+}
+
+// ---- metrics ----------------------------------------------------------------------------
+
+// Largest principal angle between span(Q1) (rows1 x r1) and span(Q2) (rows2 x r2), rows1 <= rows2
+// (Q1 embedded with zero rows), Eq. (theta-max). Computed as arcsin(sqrt(lambda_max(E))) with
+// E = Q_b^T (I - P_a) Q_b for the side b with fewer columns, which equals
+// arccos(sigma_min(Q1^T Q2)) for orthonormal bases and keeps small angles accurate.
+template <typename T>
+isvd_status max_angle(isvd_ctx* h, const T* Q1, int64_t rows1, int r1, const T* Q2, int r2, double* theta) {
+  isvd_status s;
+  double* C = h->small;              // r1 x r2
+  double* B = h->small + kSmall;     // q x q
+  double* E = h->small + 2 * kSmall; // q x q
+  double* evecs = h->small + 3 * kSmall;
+  if ((s = gemm_tn<T>(h, Q1, h->ld, r1, Q2, h->ld, r2, rows1, C))) return s;
+  const int tr = r1 <= r2 ? 1 : 0;  // E on the Q1 side when it has fewer columns
+  const int q = tr ? r1 : r2;
+  if (tr) {
+    if ((s = gemm_tn<T>(h, Q1, h->ld, r1, Q1, h->ld, r1, rows1, B))) return s;
+  } else {
+    if ((s = gemm_tn<T>(h, Q2, h->ld, r2, Q2, h->ld, r2, h->m, B))) return s;
+  }
+  k_angle_matrix<<<1, 256, 0, h->stream>>>(B, C, r1, r2, tr, E);
+  CKL(h);
+  if ((s = sym_eig<T>(h, E, q, h->evals, evecs, sizeof(T) == sizeof(double)))) return s;
+  double lam = 0;
+  CK(h, cudaMemcpyAsync(&lam, h->evals, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  lam = std::min(1.0, std::max(0.0, lam));
+  *theta = std::asin(std::sqrt(lam));
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
+  isvd_status s;
+  DevState ds;
+  if ((s = read_state(h, &ds))) return s;
+  const int r = ds.r;
+  std::vector<double> sg(r);
+  CK(h, cudaMemcpy(sg.data(), h->sig, r * 8, cudaMemcpyDeviceToHost));
+  memset(mt, 0, sizeof(*mt));
+  mt->t = h->t;
+  mt->m = h->m;
+  mt->n = h->n;
+  mt->r = r;
+  mt->k = ds.k;
+  double ss = 0;
+  for (double v : sg) ss += v * v;
+  mt->N = ds.N;
+  mt->evr = ds.N > 0 ? ss / ds.N : NAN;
+  mt->rho_last = ds.rho;
+  mt->novelty_last = ds.novelty;
+  mt->orth_err_u = h->orth_err_u;
+  mt->orth_err_v = h->orth_err_v;
+  mt->refreshes = h->refreshes;
+  mt->reorths = h->reorths;
+  mt->t_last = h->t_last;
+  const double nan = std::nan("");
+  mt->frob_error = mt->frob_opt = mt->frob_gap = mt->frob_ratio = mt->angle = mt->angle_to_opt = nan;
+  if (!(flags & ISVD_METRICS_FULL)) return ISVD_OK;
+  // E_inc
+  CK(h, cudaMemsetAsync(h->scal, 0, 8, h->stream));
+  {
+    dim3 grid((unsigned)((h->n + kResTile - 1) / kResTile), (unsigned)((h->m + kResTile - 1) / kResTile));
+    const size_t sm = (size_t)2 * std::max(r, 1) * (kResTile + 1) * sizeof(T);
+    k_resid_norm<T><<<grid, 256, sm, h->stream>>>((const T*)h->A, h->col_cap, h->m, h->n, (const T*)h->U,
+                                                  (const T*)h->V, h->ld, h->sig, h->st, h->scal);
+    CKL(h);
+  }
+  // optimal rank-r factorisation
+  if ((s = ensure_buf(h, &h->Uopt, &h->uopt_cap, h->m * h->ld * (int64_t)h->es))) return s;
+  if ((s = ensure_buf(h, &h->Vopt, &h->vopt_cap, h->n * h->ld * (int64_t)h->es))) return s;
+  if ((s = tsvd<T>(h, r, (T*)h->Uopt, h->sig_opt, (T*)h->Vopt))) return s;
+  double sc[2];
+  CK(h, cudaMemcpyAsync(sc, h->scal, 16, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const double e_inc = std::sqrt(std::max(sc[0], 0.0));
+  const double e_opt = std::sqrt(std::max(sc[1], 0.0));
+  mt->frob_error = e_inc;
+  mt->frob_opt = e_opt;
+  mt->frob_gap = e_inc - e_opt;
+  mt->frob_ratio = (e_opt <= 1e-12 * std::sqrt(std::max(ds.N, 0.0))) ? nan : e_inc / e_opt;
+  double th = nan;
+  if ((s = max_angle<T>(h, (const T*)h->Uopt, h->m, r, (const T*)h->U, r, &th))) return s;
+  mt->angle_to_opt = th;
+  if (h->Uref && h->r_ref > 0) {
+    if ((s = max_angle<T>(h, (const T*)h->Uref, h->m_ref, h->r_ref, (const T*)h->U, r, &th))) return s;
+    mt->angle = th;
+  }
+  return ISVD_OK;
+}
+
+// ---- re-orthogonalisation -----------------------------------------------------------------
+
+template <typename T>
+isvd_status orth_err(isvd_ctx* h, const T* Q, int64_t rows, int r, double* err) {
+  isvd_status s;
+  double* B = h->small + 4 * kSmall;
+  if ((s = gemm_tn<T>(h, Q, h->ld, r, Q, h->ld, r, rows, B))) return s;
+  k_max_offident<<<1, 256, 0, h->stream>>>(B, r, h->scal + 2);
+  CKL(h);
+  CK(h, cudaMemcpyAsync(err, h->scal + 2, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return ISVD_OK;
+}
+
+// One Cholesky-QR pass Q <- Q R^-1 with R^T R = Q^T Q (B must hold Q^T Q).
+template <typename T>
+isvd_status cholqr_pass(isvd_ctx* h, T* Q, int64_t rows, int r) {
+  isvd_status s;
+  double* B = h->small + 4 * kSmall;
+  if ((s = gemm_tn<T>(h, Q, h->ld, r, Q, h->ld, r, rows, B))) return s;
+  k_chol_rinv<T><<<1, 128, (size_t)r * r * sizeof(double), h->stream>>>(B, r, h->small + 5 * kSmall, (T*)h->Rtmp,
+                                                                          h->ld, h->info);
+  CKL(h);
+  RotSide sq{};
+  sq.X = sq.Y = Q;
+  sq.rows = rows;
+  sq.ldx = sq.ldy = h->ld;
+  sq.R = h->Rtmp;
+  sq.ldr = h->ld;
+  sq.c_in = r;
+  sq.k_out = r;
+  RotSide none{};
+  return launch_rotate<T>(h, sq, none, kb_bucket(h->kmax), (const T*)nullptr, nullptr);
+}
+
+template <typename T>
+isvd_status do_reorth(isvd_ctx* h, int force, double* eu, double* ev) {
+  isvd_status s;
+  DevState ds;
+  if ((s = read_state(h, &ds))) return s;
+  const int r = ds.r;
+  if ((s = orth_err<T>(h, (const T*)h->U, h->m, r, &h->orth_err_u))) return s;
+  if ((s = orth_err<T>(h, (const T*)h->V, h->n, r, &h->orth_err_v))) return s;
+  if (force || h->orth_err_u > h->orth_tol || h->orth_err_v > h->orth_tol) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((s = cholqr_pass<T>(h, (T*)h->U, h->m, r))) return s;
+      if ((s = cholqr_pass<T>(h, (T*)h->V, h->n, r))) return s;
+    }
+    h->reorths++;
+  }
+  if (eu) *eu = h->orth_err_u;
+  if (ev) *ev = h->orth_err_v;
+  h->since_orth = 0;
+  return ISVD_OK;
+}
+
+// ---- policy (Section 3), evaluated after every update -------------------------------------
+
+template <typename T>
+isvd_status after_update(isvd_ctx* h) {
+  h->t += 1;
+  h->since_orth += 1;
+  isvd_status s;
+  bool fire = false;
+  if (h->has_pol) {
+    const isvd_policy& pol = h->pol;
+    if ((pol.kind & ISVD_POLICY_PERIODIC) && pol.T_refresh > 0 && h->t % pol.T_refresh == 0) fire = true;
+    if (pol.check_every > 0 && h->t % pol.check_every == 0) {
+      isvd_metrics_t mt;
+      prof_begin(h, ISVD_KCLASS_CHECK, 0.0);
+      if ((s = do_metrics<T>(h, ISVD_METRICS_FULL, &mt))) return s;
+      prof_end(h);
+      const bool spaced = (h->t - h->t_last) >= pol.T_min;
+      if ((pol.kind & ISVD_POLICY_ERROR) && spaced && std::isfinite(mt.frob_ratio) && mt.frob_ratio > pol.gamma)
+        fire = true;
+      if ((pol.kind & ISVD_POLICY_ANGLE) && spaced && std::isfinite(mt.angle_to_opt) &&
+          mt.angle_to_opt > pol.theta_max_rad)
+        fire = true;
+      if ((pol.kind & ISVD_POLICY_ADAPTIVE_RANK) && std::isfinite(mt.evr) && mt.evr < pol.tau_evr) {
+        const int kcap = pol.k_max > 0 ? std::min(pol.k_max, h->kmax) : h->kmax;
+        const int knew = std::min(h->k_host + 1, kcap);
+        if (knew != h->k_host) {
+          h->k_host = knew;
+          CK(h, cudaMemcpyAsync(&h->st->k, &h->k_host, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+          CK(h, cudaStreamSynchronize(h->stream));
+        }
+      }
+      h->last_check = mt;
+    }
+  }
+  if (fire) {
+    prof_begin(h, ISVD_KCLASS_REFRESH, 0.0);
+    if ((s = do_refresh<T>(h, h->has_pol ? h->pol.store_initial_subspace : 0))) return s;
+    prof_end(h);
+    if (h->has_pol && h->pol.check_every > 0 && h->t % h->pol.check_every == 0) h->last_check.t_last = h->t;
+  }
+  if (h->orth_every > 0 && h->since_orth >= h->orth_every) {
+    prof_begin(h, ISVD_KCLASS_REORTH, 0.0);
+    if ((s = do_reorth<T>(h, 0, nullptr, nullptr))) return s;
+    prof_end(h);
+  }
+  prof_stamp(h);
+  return ISVD_OK;
+}
+
+// ---- host vector staging ------------------------------------------------------------------
+
+isvd_status stage(isvd_ctx* h, const void* src, int64_t len, int on_device, const void** out) {
+  if (on_device) {
+    *out = src;
+    return ISVD_OK;
+  }
+  isvd_status s;
+  // The previous update may still read xbuf: wait for the stream before overwriting it.
+  const int64_t bytes = len * (int64_t)h->es;
+  if (bytes > h->xbuf_cap) {
+    if ((s = ensure_buf(h, &h->xbuf, &h->xbuf_cap, bytes))) return s;
+  }
+  CK(h, cudaMemcpyAsync(h->xbuf, src, (size_t)bytes, cudaMemcpyHostToDevice, h->stream));
+  *out = h->xbuf;
+  return ISVD_OK;
+}
+
+template <typename T>
+isvd_status create_impl(isvd_ctx* h, const void* A0, int64_t m0, int64_t n0, int64_t lda0, int k, int on_dev,
+                        const void* U0 = nullptr, const double* S0 = nullptr, const void* V0 = nullptr) {
+  isvd_status s;
+  if ((s = set_attrs<T>(h))) return s;
+  if ((s = dmalloc(h, &h->U, (size_t)h->row_cap * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, &h->V, (size_t)h->col_cap * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, &h->A, (size_t)h->row_cap * h->col_cap * h->es))) return s;
+  if ((s = dmalloc(h, (void**)&h->st, sizeof(DevState)))) return s;
+  if ((s = dmalloc(h, (void**)&h->sig, (kKmaxLimit + 2) * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->p, (kKmaxLimit + 2) * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->part, (size_t)kMaxProjBlocks * kPartStride * 8))) return s;
+  if ((s = dmalloc(h, &h->UK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, &h->VK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
+  if ((s = dmalloc(h, (void**)&h->small, (size_t)6 * kSmall * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->evals, (kKmaxLimit + 2) * 8 * 2))) return s;
+  if ((s = dmalloc(h, (void**)&h->inv, (kKmaxLimit + 2) * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->sig_opt, (kKmaxLimit + 2) * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->scal, 64))) return s;
+  if ((s = dmalloc(h, (void**)&h->info, 64))) return s;
+  if ((s = dmalloc(h, &h->Rtmp, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
+  CK(h, cudaMemsetAsync(h->U, 0, (size_t)h->row_cap * h->ld * h->es, h->stream));
+  CK(h, cudaMemsetAsync(h->V, 0, (size_t)h->col_cap * h->ld * h->es, h->stream));
+  CK(h, cudaMemcpy2DAsync(h->A, h->col_cap * h->es, A0, lda0 * h->es, n0 * h->es, m0,
+                          on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  h->m = m0;
+  h->n = n0;
+  // N_0 = ||A0||_F^2 (Section 2.4): the trace of the Gram of A0 through the same product kernel.
+  DevState ds{};
+  ds.k = k;
+  CK(h, cudaMemcpyAsync(h->st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemsetAsync(h->scal, 0, 64, h->stream));
+  {
+    // sum of squares via the residual kernel with r = 0 (E = ||A - 0||).
+    dim3 grid((unsigned)((n0 + kResTile - 1) / kResTile), (unsigned)((m0 + kResTile - 1) / kResTile));
+    k_resid_norm<T><<<grid, 256, (size_t)2 * (kResTile + 1) * sizeof(T), h->stream>>>(
+        (const T*)h->A, h->col_cap, m0, n0, (const T*)h->U, (const T*)h->V, h->ld, h->sig, h->st, h->scal);
+    CKL(h);
+  }
+  CK(h, cudaMemcpyAsync(&h->st->N, h->scal, 8, cudaMemcpyDeviceToDevice, h->stream));
+  const int r0 = (int)std::min<int64_t>(k, std::min(m0, n0));
+  if (U0) {
+    // Caller-supplied initial factors (U0 m0 x r0, sigma0 r0, V0 n0 x r0, row stride r0).
+    const cudaMemcpyKind kd = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(h, cudaMemcpy2DAsync(h->U, h->ld * h->es, U0, r0 * h->es, r0 * h->es, m0, kd, h->stream));
+    CK(h, cudaMemcpy2DAsync(h->V, h->ld * h->es, V0, r0 * h->es, r0 * h->es, n0, kd, h->stream));
+    CK(h, cudaMemcpyAsync(h->sig, S0, r0 * 8, kd, h->stream));
+  } else {
+    if ((s = tsvd<T>(h, r0, (T*)h->U, h->sig, (T*)h->V, 0))) return s;
+  }
+  if ((s = set_rank<T>(h, r0))) return s;
+  if ((s = store_ref<T>(h, r0))) return s;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return read_state(h, &ds);
+}
+
+}  // namespace
+
+// ---- C ABI ----------------------------------------------------------------------------------
+
+extern "C" {
+
+const char* isvd_status_string(isvd_status s) {
+  switch (s) {
+    case ISVD_OK: return "ok";
+    case ISVD_EINVAL: return "invalid argument";
+    case ISVD_ESHAPE: return "shape mismatch";
+    case ISVD_EBOUNDS: return "index out of bounds";
+    case ISVD_ENOMEM: return "out of device memory";
+    case ISVD_EBUDGET: return "memory budget exceeded";
+    case ISVD_ENOTCONV: return "core SVD did not converge";
+    case ISVD_ETIMEOUT: return "device wait timed out";
+    case ISVD_ECUDA: return "CUDA error";
+    case ISVD_ENONFINITE: return "non-finite input";
+  }
+  return "unknown status";
+}
+
+static isvd_status create_common(const isvd_config* cfg, const void* A0, int64_t m0, int64_t n0, int64_t lda, int k,
+                                 int on_dev, const void* U0, const double* S0, const void* V0, int r0, isvd_t* out) {
+  if (!cfg || !A0 || !out) return ISVD_EINVAL;
+  *out = nullptr;
+  if (m0 < 1 || n0 < 1 || lda < n0 || k < 1) return ISVD_ESHAPE;
+  if (cfg->prec != ISVD_FP64 && cfg->prec != ISVD_FP32) return ISVD_EINVAL;
+  const int kmax = cfg->k_max > 0 ? cfg->k_max : k;
+  if (kmax < k || kmax > kKmaxLimit) return ISVD_EINVAL;
+  if (cfg->prec == ISVD_FP64 && kmax > 96) return ISVD_EINVAL;  // FP64 core shared memory
+  if (U0 && (!S0 || !V0 || r0 != (int)std::min<int64_t>(k, std::min(m0, n0)))) return ISVD_ESHAPE;
+  isvd_ctx* h = new isvd_ctx();
+  h->prec = cfg->prec;
+  h->es = cfg->prec == ISVD_FP64 ? 8 : 4;
+  h->stream = (cudaStream_t)cfg->cuda_stream;
+  cudaGetDevice(&h->dev);
+  h->kmax = kmax;
+  h->ld = round_up(kmax, 4);
+  h->k_host = k;
+  h->tol_rel = cfg->tol_rel > 0 ? cfg->tol_rel : (cfg->prec == ISVD_FP64 ? 1e-10 : 3e-6);
+  h->orth_tol = cfg->orth_tol > 0 ? cfg->orth_tol : (cfg->prec == ISVD_FP64 ? 1e-12 : 1e-5);
+  h->orth_every = cfg->orth_every > 0 ? cfg->orth_every : (cfg->prec == ISVD_FP64 ? 0 : 256);
+  h->row_cap = std::max<int64_t>(cfg->row_cap > 0 ? cfg->row_cap : 2 * m0, m0 + 1);
+  h->col_cap = std::max<int64_t>(cfg->col_cap > 0 ? cfg->col_cap : 2 * n0, n0 + 1);
+  h->rsvd_p = cfg->rsvd_oversample > 0 ? cfg->rsvd_oversample : 16;
+  h->rsvd_q = cfg->rsvd_power_iters >= 0 ? cfg->rsvd_power_iters : 2;
+  h->seed = cfg->seed;
+  if (!on_dev) {
+    bool ok = true;
+    for (int64_t i = 0; i < m0 && ok; ++i)
+      ok = h->prec == ISVD_FP64 ? host_finite((const double*)A0 + i * lda, n0) : host_finite((const float*)A0 + i * lda, n0);
+    if (!ok) {
+      delete h;
+      return ISVD_ENONFINITE;
+    }
+  }
+  isvd_status s = h->prec == ISVD_FP64 ? create_impl<double>(h, A0, m0, n0, lda, k, on_dev, U0, S0, V0)
+                                       : create_impl<float>(h, A0, m0, n0, lda, k, on_dev, U0, S0, V0);
+  if (s != ISVD_OK) {
+    fprintf(stderr, "isvd_create: %s\n", h->err.c_str());
+    isvd_destroy(h);
+    return s;
+  }
+  *out = h;
+  return ISVD_OK;
+}
+
+isvd_status isvd_create(const isvd_config* cfg, const void* A0, int64_t m0, int64_t n0, int64_t lda, int k,
+                        int a0_on_device, isvd_t* out) {
+  return create_common(cfg, A0, m0, n0, lda, k, a0_on_device, nullptr, nullptr, nullptr, 0, out);
+}
+
+isvd_status isvd_create_from_factors(const isvd_config* cfg, const void* A0, int64_t m0, int64_t n0, int64_t lda,
+                                     const void* U0, const double* sigma0, const void* V0, int r0, int k,
+                                     int on_device, isvd_t* out) {
+  if (!U0) return ISVD_EINVAL;
+  return create_common(cfg, A0, m0, n0, lda, k, on_device, U0, sigma0, V0, r0, out);
+}
+
+void isvd_destroy(isvd_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  void* bufs[] = {h->U, h->V, h->A, h->Uref, h->st, h->sig, h->p, h->part, h->UK, h->VK, h->xbuf, h->G,
+                  h->small, h->evals, h->inv, h->scal, h->info, h->Rtmp, h->Uopt, h->Vopt, h->sig_opt, h->Cbuf,
+                  h->Yb, h->Om, h->Zd, h->Rl};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+static isvd_status append_common(isvd_t h, int kind, const void* v, int64_t len, int on_device) {
+  if (!h || !v) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  const int64_t want = kind == kRow ? h->n : h->m;
+  if (len != want) return fail(h, ISVD_ESHAPE, "vector length " + std::to_string(len) + " != " + std::to_string(want));
+  if (!on_device) {
+    const bool ok = h->prec == ISVD_FP64 ? host_finite((const double*)v, len) : host_finite((const float*)v, len);
+    if (!ok) return fail(h, ISVD_ENONFINITE, "non-finite value in the appended vector");
+  }
+  const void* dv = nullptr;
+  isvd_status s = stage(h, v, len, on_device, &dv);
+  if (s) return s;
+  s = h->prec == ISVD_FP64 ? do_append<double>(h, kind, (const double*)dv) : do_append<float>(h, kind, (const float*)dv);
+  if (s) return s;
+  return h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h);
+}
+
+isvd_status isvd_append_row(isvd_t h, const void* x, int64_t n, int on_device) {
+  return append_common(h, kRow, x, n, on_device);
+}
+
+isvd_status isvd_append_col(isvd_t h, const void* y, int64_t m, int on_device) {
+  return append_common(h, kCol, y, m, on_device);
+}
+
+isvd_status isvd_update_entry(isvd_t h, int64_t i, int64_t j, double delta) {
+  if (!h) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  if (i < 0 || i >= h->m || j < 0 || j >= h->n) return fail(h, ISVD_EBOUNDS, "entry index out of range");
+  if (!std::isfinite(delta)) return fail(h, ISVD_ENONFINITE, "non-finite delta");
+  isvd_status s = h->prec == ISVD_FP64 ? do_entry<double>(h, i, j, delta) : do_entry<float>(h, i, j, delta);
+  if (s) return s;
+  return h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h);
+}
+
+isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload, int64_t payload_len,
+                              int payload_on_device) {
+  if (!h || (nev > 0 && !ev)) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  isvd_status s;
+  const char* base = (const char*)payload;
+  if (!payload_on_device && payload_len > 0) {
+    // One host-to-device copy of the whole payload; the events then read it in place.
+    const bool ok = h->prec == ISVD_FP64 ? host_finite((const double*)payload, payload_len)
+                                         : host_finite((const float*)payload, payload_len);
+    if (!ok) return fail(h, ISVD_ENONFINITE, "non-finite value in the event payload");
+    if ((s = ensure_buf(h, &h->xbuf, &h->xbuf_cap, payload_len * (int64_t)h->es))) return s;
+    CK(h, cudaMemcpyAsync(h->xbuf, payload, (size_t)payload_len * h->es, cudaMemcpyHostToDevice, h->stream));
+    base = (const char*)h->xbuf;
+  }
+  for (int64_t e = 0; e < nev; ++e) {
+    const isvd_event& E = ev[e];
+    if (E.kind == kEntry) {
+      if ((s = isvd_update_entry(h, E.i, E.j, E.delta))) return s;
+      continue;
+    }
+    if (E.kind != kRow && E.kind != kCol) return fail(h, ISVD_EINVAL, "unknown event kind");
+    const int64_t want = E.kind == kRow ? h->n : h->m;
+    if (E.len != want) return fail(h, ISVD_ESHAPE, "event vector length mismatch");
+    if (E.off < 0 || E.off + E.len > payload_len) return fail(h, ISVD_EBOUNDS, "event payload out of range");
+    const void* dv = base + E.off * (int64_t)h->es;
+    s = h->prec == ISVD_FP64 ? do_append<double>(h, E.kind, (const double*)dv) : do_append<float>(h, E.kind, (const float*)dv);
+    if (s) return s;
+    if ((s = (h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h)))) return s;
+  }
+  return ISVD_OK;
+}
+
+isvd_status isvd_set_policy(isvd_t h, const isvd_policy* pol) {
+  if (!h) return ISVD_EINVAL;
+  if (!pol) {
+    h->has_pol = 0;
+    return ISVD_OK;
+  }
+  if (pol->T_refresh < 0 || pol->T_min < 0 || pol->check_every < 0) return ISVD_EINVAL;
+  if (pol->k_max > h->kmax) return fail(h, ISVD_EINVAL, "policy k_max exceeds the handle's k_max");
+  h->pol = *pol;
+  h->has_pol = 1;
+  return ISVD_OK;
+}
+
+isvd_status isvd_refresh(isvd_t h, int store_initial_subspace) {
+  if (!h) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  return h->prec == ISVD_FP64 ? do_refresh<double>(h, store_initial_subspace) : do_refresh<float>(h, store_initial_subspace);
+}
+
+isvd_status isvd_metrics(isvd_t h, int flags, isvd_metrics_t* out) {
+  if (!h || !out) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  if (flags & ~ISVD_METRICS_FULL) return ISVD_EINVAL;
+  return h->prec == ISVD_FP64 ? do_metrics<double>(h, flags, out) : do_metrics<float>(h, flags, out);
+}
+
+isvd_status isvd_last_check_metrics(isvd_t h, isvd_metrics_t* out) {
+  if (!h || !out) return ISVD_EINVAL;
+  *out = h->last_check;
+  return ISVD_OK;
+}
+
+isvd_status isvd_get_shape(isvd_t h, int64_t* m, int64_t* n, int32_t* r, int32_t* k) {
+  if (!h) return ISVD_EINVAL;
+  DevState ds;
+  isvd_status s = read_state(h, &ds);
+  if (s) return s;
+  if (m) *m = h->m;
+  if (n) *n = h->n;
+  if (r) *r = ds.r;
+  if (k) *k = ds.k;
+  return ISVD_OK;
+}
+
+isvd_status isvd_get_factors(isvd_t h, void* U, double* sigma, void* V, int to_device) {
+  if (!h) return ISVD_EINVAL;
+  DevState ds;
+  isvd_status s = read_state(h, &ds);
+  if (s) return s;
+  const int r = ds.r;
+  const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (U) CK(h, cudaMemcpy2DAsync(U, r * h->es, h->U, h->ld * h->es, r * h->es, h->m, kind, h->stream));
+  if (V) CK(h, cudaMemcpy2DAsync(V, r * h->es, h->V, h->ld * h->es, r * h->es, h->n, kind, h->stream));
+  if (sigma) CK(h, cudaMemcpyAsync(sigma, h->sig, r * 8, to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return ISVD_OK;
+}
+
+isvd_status isvd_get_matrix(isvd_t h, void* A, int to_device) {
+  if (!h || !A) return ISVD_EINVAL;
+  const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(h, cudaMemcpy2DAsync(A, h->n * h->es, h->A, h->col_cap * h->es, h->n * h->es, h->m, kind, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return ISVD_OK;
+}
+
+isvd_status isvd_reorthogonalize(isvd_t h, int force, double* err_u, double* err_v) {
+  if (!h) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  return h->prec == ISVD_FP64 ? do_reorth<double>(h, force, err_u, err_v) : do_reorth<float>(h, force, err_u, err_v);
+}
+
+isvd_status isvd_sync(isvd_t h) {
+  if (!h) return ISVD_EINVAL;
+  DevState ds;
+  return read_state(h, &ds);
+}
+
+int64_t isvd_kernel_launches(isvd_t h) { return h ? h->launches : 0; }
+
+isvd_status isvd_profile(isvd_t h, int enable) {
+  if (!h) return ISVD_EINVAL;
+  prof_flush(h);
+  h->prof = enable ? 1 : 0;
+  for (int c = 0; c < ISVD_NUM_KCLASS; ++c) {
+    h->cls_ms[c] = 0;
+    h->cls_bytes[c] = 0;
+    h->cls_n[c] = 0;
+  }
+  h->lat_us.clear();
+  h->stamps.clear();
+  h->spans.clear();
+  h->ev_used = 0;
+  if (h->prof) prof_stamp(h);
+  return ISVD_OK;
+}
+
+isvd_status isvd_profile_read(isvd_t h, int cls, double* total_ms, double* bytes, int64_t* launches) {
+  if (!h || cls < 0 || cls >= ISVD_NUM_KCLASS) return ISVD_EINVAL;
+  prof_flush(h);
+  if (total_ms) *total_ms = h->cls_ms[cls];
+  if (bytes) *bytes = h->cls_bytes[cls];
+  if (launches) *launches = h->cls_n[cls];
+  return ISVD_OK;
+}
+
+isvd_status isvd_latencies(isvd_t h, double* us, int64_t cap, int64_t* count) {
+  if (!h || !count) return ISVD_EINVAL;
+  prof_flush(h);
+  const int64_t n = (int64_t)h->lat_us.size();
+  *count = n;
+  if (us) memcpy(us, h->lat_us.data(), sizeof(double) * (size_t)std::min(n, cap));
+  return ISVD_OK;
+}
+
+const char* isvd_last_error(isvd_t h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

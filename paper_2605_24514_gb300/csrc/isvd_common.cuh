@@ -1,0 +1,63 @@
+// Shared device-side definitions of libisvd (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isvd {
+
+// Largest supported working-rank capacity (columns of U and V).
+constexpr int kKmaxLimit = 128;
+// Partial-sum slots per projection pass (blocks of the projection kernels).
+constexpr int kMaxProjBlocks = 256;
+
+// Sticky device status bits (mapped to isvd_status on the host).
+constexpr int kStNotConv = 1;
+constexpr int kStNonFinite = 2;
+constexpr int kStTimeout = 4;
+
+// Update kinds (Section 2.1).
+constexpr int kRow = 0;
+constexpr int kCol = 1;
+constexpr int kEntry = 2;
+
+// Device-resident scalar state of one stream; read and written only by kernels, so a
+// sequence of updates needs no host round trip.
+struct DevState {
+  int32_t r;          // maintained rank r_t
+  int32_t k;          // working rank k_t
+  int32_t status;     // sticky error bits
+  int32_t grew;       // last append kept its new direction (rho > tol)
+  int32_t r_in;       // rank before the last core SVD
+  int32_t k_out;      // rank after it
+  int32_t sweeps;     // Jacobi sweeps of the last core SVD
+  int32_t pad0;
+  double N;           // N_t = ||A_t||_F^2
+  double xnorm2;      // ||x||^2 of the last append
+  double rho;         // residual norm of the last append
+  double novelty;     // rho / ||x||
+  unsigned int counter;   // last-block-done counter of the projection kernels
+  unsigned int pad1;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T half_sum(T v) {  // sum over aligned groups of 16 lanes
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr float v = 5.9604645e-8f; };
+template <> struct Eps<double> { static constexpr double v = 1.1102230246251565e-16; };
+
+__device__ __forceinline__ bool is_finite_d(double x) { return isfinite(x); }
+
+}  // namespace isvd

@@ -40,13 +40,14 @@ class FactorModel:
     nu: float = 4.0
     rng: np.random.Generator = field(init=False, repr=False)
     B: np.ndarray = field(init=False, repr=False)
-    F_hist: list = field(init=False, repr=False)
+    F: np.ndarray = field(init=False, repr=False)
+    t: int = field(init=False, default=0)
 
     def __post_init__(self):
         self.rng = np.random.Generator(np.random.PCG64(self.seed))
         self.vol = 0.02 * 0.7 ** np.arange(self.f)
         self.B = self.rng.standard_normal((self.n, self.f)) / np.sqrt(self.f)
-        self.F_hist = []
+        self.F = np.zeros((64, self.f))
 
     def _noise(self, size):
         if self.noise == "gauss":
@@ -58,14 +59,19 @@ class FactorModel:
     def rows(self, t: int) -> np.ndarray:
         """Draw ``t`` new time steps (rows) over the current asset set."""
         Fn = self.rng.standard_normal((t, self.f)) * self.vol
-        self.F_hist.extend(Fn)
+        if self.t + t > self.F.shape[0]:
+            F2 = np.zeros((max(2 * self.F.shape[0], self.t + t), self.f))
+            F2[:self.t] = self.F[:self.t]
+            self.F = F2
+        self.F[self.t:self.t + t] = Fn
+        self.t += t
         return Fn @ self.B.T + self._noise((t, self.B.shape[0]))
 
     def new_asset(self) -> np.ndarray:
         """Draw one new asset (column) over the stored factor history."""
         b = self.rng.standard_normal(self.f) / np.sqrt(self.f)
         self.B = np.vstack([self.B, b[None, :]])
-        F = np.asarray(self.F_hist).reshape(-1, self.f)
+        F = self.F[:self.t]
         return F @ b + self._noise(F.shape[0])
 
 
@@ -151,6 +157,7 @@ def make_events(fm: FactorModel, m0: int, n_events: int, mix=(1.0, 0.0, 0.0),
             pos += v.size
             n += 1
         else:
+            off[e] = pos   # zero-length payload at the current position
             ii[e] = rng.integers(0, m)
             jj[e] = rng.integers(0, n)
             dd[e] = delta_sd * rng.standard_normal()
