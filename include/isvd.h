@@ -112,6 +112,8 @@ typedef struct {
   int64_t refreshes;     /* refreshes performed */
   int64_t reorths;       /* re-orthogonalisations performed */
   int64_t t_last;        /* time of the last refresh */
+  int32_t core_sweeps;   /* Jacobi sweeps of the last core SVD (-1: not converged) */
+  int32_t reserved0;
 } isvd_metrics_t;
 
 /* Flags of isvd_metrics. */

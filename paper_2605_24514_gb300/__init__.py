@@ -53,7 +53,8 @@ class Metrics(C.Structure):
                 ("frob_ratio", C.c_double), ("angle", C.c_double), ("angle_to_opt", C.c_double),
                 ("evr", C.c_double), ("rho_last", C.c_double), ("novelty_last", C.c_double),
                 ("orth_err_u", C.c_double), ("orth_err_v", C.c_double), ("N", C.c_double),
-                ("refreshes", C.c_int64), ("reorths", C.c_int64), ("t_last", C.c_int64)]
+                ("refreshes", C.c_int64), ("reorths", C.c_int64), ("t_last", C.c_int64),
+                ("core_sweeps", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -185,11 +185,20 @@ isvd_status fail(isvd_ctx* h, isvd_status s, const std::string& msg) {
 int kb_bucket(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+template <typename T>
+size_t core_kernel_smem(int kmax) {
+  size_t b = core_smem_bytes<T>(kmax);
+  if (sizeof(T) == sizeof(float)) b = std::max(b, core_fast_smem_bytes<T>(kmax));
+  return 2 * (kKmaxLimit + 1) * sizeof(double) + b;
+}
+
 int core_threads(int kmax) {
+  // Enough 8-lane groups for one root per group in the secular solver (kmax + 1 roots), which
+  // also covers the Jacobi pairs; capped by the kernel's launch bound.
   const int nc = kmax + 1;
-  const int npairs = (nc + 1) / 2;
-  int warps = (npairs + 1) / 2;
-  warps = std::max(2, std::min(32, warps));
+  int warps = (nc * kSecLanes + 31) / 32;
+  const int cap = core_max_threads(kb_bucket(kmax)) / 32;
+  warps = std::max(2, std::min(cap, warps));
   return warps * 32;
 }
 
@@ -198,6 +207,26 @@ bool host_finite(const T* v, int64_t len) {
   for (int64_t i = 0; i < len; ++i)
     if (!std::isfinite((double)v[i])) return false;
   return true;
+}
+
+// One launch of the core SVD kernel (single CTA), templated on the rank bucket.
+template <typename T>
+isvd_status launch_core(isvd_ctx* h, int kind, int64_t i, int64_t j, double delta) {
+  const size_t cs = core_kernel_smem<T>(h->kmax);
+  const int th = core_threads(h->kmax);
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  T* A = (T*)h->A;
+#define ISVD_CORE_ARGS kind, h->st, h->sig, h->p, U, V, h->ld, i, j, delta, A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld
+  switch (kb_bucket(h->kmax)) {
+    case 16: k_core<T, T, 16><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
+    case 32: k_core<T, T, 32><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
+    case 64: k_core<T, T, 64><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
+    default: k_core<T, T, 128><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
+  }
+#undef ISVD_CORE_ARGS
+  CKL(h);
+  return ISVD_OK;
 }
 
 template <typename T, int KB>
@@ -212,9 +241,11 @@ isvd_status set_attrs(isvd_ctx* h) {
   if ((s = set_rot_attr<T, 16>(h)) || (s = set_rot_attr<T, 32>(h)) || (s = set_rot_attr<T, 64>(h)) ||
       (s = set_rot_attr<T, 128>(h)))
     return s;
-  using JT = T;
-  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<JT>(h->kmax);
-  CK(h, cudaFuncSetAttribute(k_core<T, JT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  const size_t cs = core_kernel_smem<T>(h->kmax);
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
   CK(h, cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_chol_rinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -361,11 +392,8 @@ isvd_status do_append(isvd_ctx* h, int kind, const T* x) {
   }
   CKL(h);
   prof_end(h);
-  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<T>(h->kmax);
   prof_begin(h, ISVD_KCLASS_CORE, 2.0 * (kk + 1) * kk * h->es);
-  k_core<T, T><<<1, core_threads(h->kmax), cs, h->stream>>>(kind, h->st, h->sig, h->p, U, V, h->ld, 0, 0, 0.0, A, lda,
-                                                            (T*)h->UK, (T*)h->VK, h->ld);
-  CKL(h);
+  if ((s = launch_core<T>(h, kind, 0, 0, 0.0))) return s;
   prof_end(h);
   // Rotations. Row append: U side uses U_K plus the new row, V side uses V_K plus z_hat.
   // Column append (transpose): U side uses V_K plus z_hat, V side uses U_K plus the new row.
@@ -405,11 +433,9 @@ isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
   T* U = (T*)h->U;
   T* V = (T*)h->V;
   const double kk = (double)h->k_host;
-  const size_t cs = 2 * (kKmaxLimit + 1) * sizeof(double) + core_smem_bytes<T>(h->kmax);
   prof_begin(h, ISVD_KCLASS_CORE, 2.0 * kk * kk * h->es);
-  k_core<T, T><<<1, core_threads(h->kmax), cs, h->stream>>>(kEntry, h->st, h->sig, h->p, U, V, h->ld, i, j, delta,
-                                                            (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld);
-  CKL(h);
+  isvd_status s0 = launch_core<T>(h, kEntry, i, j, delta);
+  if (s0) return s0;
   prof_end(h);
   RotSide su{}, sv{};
   su.X = su.Y = U;
@@ -719,6 +745,7 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   mt->refreshes = h->refreshes;
   mt->reorths = h->reorths;
   mt->t_last = h->t_last;
+  mt->core_sweeps = ds.sweeps;
   const double nan = std::nan("");
   mt->frob_error = mt->frob_opt = mt->frob_gap = mt->frob_ratio = mt->angle = mt->angle_to_opt = nan;
   if (!(flags & ISVD_METRICS_FULL)) return ISVD_OK;
@@ -1172,6 +1199,12 @@ isvd_status isvd_sync(isvd_t h) {
 }
 
 int64_t isvd_kernel_launches(isvd_t h) { return h ? h->launches : 0; }
+
+#ifdef ISVD_CORE_TIMING
+int isvd_debug_core_clock(long long* out) {
+  return (int)cudaMemcpyFromSymbol(out, isvd_core_clock, sizeof(long long) * 16);
+}
+#endif
 
 isvd_status isvd_profile(isvd_t h, int enable) {
   if (!h) return ISVD_EINVAL;

@@ -40,6 +40,21 @@ struct DevState {
   unsigned int pad1;
 };
 
+// Optional phase timing of the core kernel (compile with -DISVD_CORE_TIMING): thread 0 stores
+// clock64() stamps into isvd_core_clock[0..15].
+#ifdef ISVD_CORE_TIMING
+__device__ long long isvd_core_clock[16];
+#define ISVD_STAMP(i)                                                   \
+  do {                                                                  \
+    __syncthreads();                                                    \
+    if (threadIdx.x == 0) isvd_core_clock[(i)] = clock64();             \
+  } while (0)
+#else
+#define ISVD_STAMP(i) \
+  do {                \
+  } while (0)
+#endif
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -3,6 +3,7 @@
 // factors (Step 3: U' = blkdiag(U, 1) U_K, V' = [V z_hat] V_K; entry: U' = U U_K, V' = V V_K).
 #pragma once
 
+#include "core_fast.cuh"
 #include "core_svd.cuh"
 #include "isvd_common.cuh"
 
@@ -200,8 +201,12 @@ __global__ void __launch_bounds__(kProjThreads) k_proj2(const T* __restrict__ X,
 
 // Core SVD of one update (single CTA). For an entry update it first gathers s_u = U[i, :] and
 // s_v = V[j, :] and applies A_ij += delta with N_t += 2 delta A_ij + delta^2 (Section 2.5).
-template <typename T, typename JT>
-__global__ void k_core(int kind, DevState* st, double* sig, const double* __restrict__ p, const T* U,
+// Threads of the core kernel: up to 1024 for rank buckets <= 64 (so one secular-solver round covers
+// every root), 512 for the 128 bucket (register budget).
+__host__ __device__ constexpr int core_max_threads(int kb) { return kb <= 64 ? 1024 : 512; }
+
+template <typename T, typename JT, int KB>
+__global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevState* st, double* sig, const double* __restrict__ p, const T* U,
                        const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A, int64_t lda, T* UK,
                        T* VKo, int ldo) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -233,7 +238,16 @@ __global__ void k_core(int kind, DevState* st, double* sig, const double* __rest
   in.b = ab + kKmaxLimit + 1;
   in.delta = delta;
   __shared__ int s_sweeps;
-  const int k_out = core_svd_cta<T, JT>(in, core_smem, UK, VKo, ldo, sig, &s_sweeps);
+  int k_out = -1;
+  if (sizeof(JT) < sizeof(double)) {
+    // Secular-equation core (O(k^2) roots + verification); -1 means "use the Jacobi path".
+    int it = 0;
+    k_out = core_fast_cta<T, KB>(in, core_smem, UK, VKo, ldo, sig, &it);
+    if (threadIdx.x == 0) s_sweeps = 100 + it;
+    __syncthreads();
+  }
+  if (k_out < 0) k_out = core_svd_cta<T, JT>(in, core_smem, UK, VKo, ldo, sig, &s_sweeps);
+  __syncthreads();
   if (threadIdx.x == 0) {
     st->r_in = r;
     st->k_out = k_out;
