@@ -226,6 +226,29 @@ isvd_status isvd_latencies(isvd_t h, double* us, int64_t cap, int64_t* count);
 const char* isvd_last_error(isvd_t h);
 const char* isvd_status_string(isvd_status s);
 
+/* --- allocation-free orthogonality measurement ----------------------------------------------
+ * The paper has no counterpart: this is a library service for callers that cannot allocate
+ * device memory, e.g. code running under a memory pool that forbids new allocations, code that
+ * must not trigger the device synchronisation cudaMalloc/cudaFree can cause, or a process whose
+ * device allocator belongs to another framework.
+ *
+ * Computes max|Q^T Q - I| (the quantity isvd_reorthogonalize reports as err_u / err_v) for a
+ * device matrix Q (rows x r, row-major, row stride ld >= r, element type double for ISVD_FP64 or
+ * float for ISVD_FP32) and writes it to *err_out, a caller-provided DEVICE pointer, on
+ * cuda_stream (NULL = legacy default stream); the value is ready when that stream reaches it.
+ * Allocates nothing: the r x r FP64 scratch lives in a fixed 128 KiB device array inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ *  - r may be at most ISVD_NOALLOC_MAX_R (128); larger r returns ISVD_ESHAPE and does nothing.
+ *  - rows < 0, r < 1, ld < r, NULL pointers or an unknown precision return ISVD_EINVAL.
+ *  - The first call on each device looks up the scratch array's device address (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - Every call shares the one scratch array (each call clears what it needs first), so calls
+ *    whose work overlaps on the GPU race with each other; serialise them (same stream, or
+ *    events). Returns ISVD_ECUDA if a CUDA call fails. */
+#define ISVD_NOALLOC_MAX_R 128
+isvd_status isvd_orth_error_noalloc(const void* Q, int64_t rows, int32_t r, int64_t ld, int32_t prec,
+                                    double* err_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

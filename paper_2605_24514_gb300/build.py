@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libisvd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["isvd.cu"]
+SOURCES = ["isvd.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:
