@@ -170,16 +170,50 @@ __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const flo
       }
     }
     const float* dor = use_hi ? dh : dl;
-    for (int it = 0; it < 60; ++it) {
-      const bool done = !solve || (b - a) <= 2.4e-7f * b;
-      if (__all_sync(0xffffffffu, done)) break;
-      const float tm = (a > 0.f && b > 4.f * a) ? sqrtf(a) * sqrtf(b) : 0.5f * (a + b);
-      const float fv = f_eval(dor, sgn * tm);
-      if (!done) {
-        if ((fv > 0.f) == (sgn > 0.f)) b = tm;
-        else a = tm;
+    // In u = sgn * tau the function h(u) = sgn * f(sgn * u) increases from -inf at the near pole
+    // (u = 0) and the root lies in (a, b). Each step fits the near-pole model h ~ C - S / u to
+    // h and h' at the current u (S = h' u^2, C = h + h' u) and takes its root S / C, falling back
+    // to bisection (geometric when the bracket spans decades) whenever that leaves the bracket.
+    float u = 0.5f * b;
+    for (int it = 0; it < 40; ++it) {
+      float fs = 0.f, ds = 0.f;
+      if (solve) {
+        const float tau_k = sgn * u;
+#pragma unroll
+        for (int q = 0; q < kTerms; ++q) {
+          if (q < nq) {
+            const float rq = __fdividef(1.f, dor[q] - tau_k);
+            const float t1 = w2[q] * rq;
+            fs += t1;
+            ds = fmaf(t1, rq, ds);
+          }
+        }
       }
+#pragma unroll
+      for (int o = kSecLanes / 2; o > 0; o >>= 1) {
+        fs += __shfl_xor_sync(0xffffffffu, fs, o);
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+      }
+      bool done = !solve;
+      if (solve) {
+        const float h = sgn * (1.f + fs);
+        const float hp = ds;  // h'(u) = f'(tau) > 0
+        if (h == 0.f) {
+          done = true;  // exact root: keep u
+        } else {
+          if (h < 0.f) a = u;
+          else b = u;
+          const float C = h + hp * u;
+          float un = (C > 0.f) ? hp * u * u / C : -1.f;
+          if (!(un > a && un < b)) un = (a > 0.f && b > 4.f * a) ? sqrtf(a) * sqrtf(b) : 0.5f * (a + b);
+          done = fabsf(un - u) <= 1e-7f * un || (b - a) <= 2.4e-7f * b;
+          u = un;
+        }
+      }
+      if (__all_sync(0xffffffffu, done)) break;
     }
+    a = u;
+    b = u;
     const float tau = sgn * 0.5f * (a + b);
     float vq[kTerms];
     float nrm2 = 0.f;
@@ -279,42 +313,83 @@ __device__ __forceinline__ void smem_syrk(int n, int inner, const float* X, int 
   }
 }
 
-// W = K V through K's structure (column-major, W is nr x nc with column stride nr).
-__device__ __forceinline__ void structured_kv(const CoreIn& in, int nr, int nc, const float* V, float* W,
-                                              float* tmp) {
+// W = K V through K's structure (column-major, W is nr x nc with column stride nr). sf, xf, bf are
+// float copies of sigma, p (append) or delta * a (entry), and b (entry); rhof = rho.
+__device__ __forceinline__ void structured_kv(const CoreIn& in, int nr, int nc, const float* V, float* W, float* tmp,
+                                              const float* sf, const float* xf, const float* bf, float rhof) {
   const int r = in.r;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float* coef = in.kind == kEntry ? bf : xf;
+  for (int j = warp; j < nc; j += nw) {  // tmp_j = coef . V[:r, j] (+ rho V[r, j])
+    float s = 0.f;
+    for (int i = lane; i < r; i += 32) s += coef[i] * V[(size_t)j * nc + i];
+    s = warp_sum(s);
+    if (lane == 0) tmp[j] = (in.kind != kEntry && in.grew) ? s + rhof * V[(size_t)j * nc + r] : s;
+  }
+  __syncthreads();
   if (in.kind == kEntry) {
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      float s = 0.f;
-      for (int i = 0; i < r; ++i) s += (float)in.b[i] * V[(size_t)j * nc + i];
-      tmp[j] = s;
-    }
-    __syncthreads();
     for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
       const int j = idx / nr, i = idx - j * nr;
-      W[idx] = (float)in.sig[i] * V[(size_t)j * nc + i] + (float)(in.delta * in.a[i]) * tmp[j];
+      W[idx] = sf[i] * V[(size_t)j * nc + i] + xf[i] * tmp[j];
     }
   } else {
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      float s = 0.f;
-      for (int i = 0; i < r; ++i) s += (float)in.p[i] * V[(size_t)j * nc + i];
-      if (in.grew) s += (float)in.rho * V[(size_t)j * nc + r];
-      tmp[j] = s;
-    }
-    __syncthreads();
     for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
       const int j = idx / nr, i = idx - j * nr;
-      W[idx] = i < r ? (float)in.sig[i] * V[(size_t)j * nc + i] : tmp[j];
+      W[idx] = i < r ? sf[i] * V[(size_t)j * nc + i] : tmp[j];
     }
   }
   __syncthreads();
 }
 
+// S = W^T W and Q = V^T V together (2 x 2 register blocks over the upper block triangle).
+__device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, const float* V, float* S, float* Q) {
+  const int nb = (n + 1) / 2;
+  const int npairs = nb * (nb + 1) / 2;
+  for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
+    int ba = 0, rem = pidx;
+    while (rem >= nb - ba) {
+      rem -= nb - ba;
+      ++ba;
+    }
+    const int bb = ba + rem;
+    const int a0 = 2 * ba, b0 = 2 * bb;
+    const bool a1ok = a0 + 1 < n, b1ok = b0 + 1 < n;
+    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f, q00 = 0.f, q01 = 0.f, q10 = 0.f, q11 = 0.f;
+    for (int l = 0; l < nr; ++l) {
+      const float xa0 = W[(size_t)a0 * nr + l], xa1 = a1ok ? W[(size_t)(a0 + 1) * nr + l] : 0.f;
+      const float xb0 = W[(size_t)b0 * nr + l], xb1 = b1ok ? W[(size_t)(b0 + 1) * nr + l] : 0.f;
+      s00 += xa0 * xb0;
+      s01 += xa0 * xb1;
+      s10 += xa1 * xb0;
+      s11 += xa1 * xb1;
+    }
+    for (int l = 0; l < n; ++l) {
+      const float xa0 = V[(size_t)a0 * n + l], xa1 = a1ok ? V[(size_t)(a0 + 1) * n + l] : 0.f;
+      const float xb0 = V[(size_t)b0 * n + l], xb1 = b1ok ? V[(size_t)(b0 + 1) * n + l] : 0.f;
+      q00 += xa0 * xb0;
+      q01 += xa0 * xb1;
+      q10 += xa1 * xb0;
+      q11 += xa1 * xb1;
+    }
+    const float sv[4] = {s00, s01, s10, s11}, qv[4] = {q00, q01, q10, q11};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int a_ = a0 + (e >> 1), b_ = b0 + (e & 1);
+      if (a_ < n && b_ < n) {
+        S[(size_t)b_ * n + a_] = sv[e];
+        S[(size_t)a_ * n + b_] = sv[e];
+        Q[(size_t)b_ * n + a_] = qv[e];
+        Q[(size_t)a_ * n + b_] = qv[e];
+      }
+    }
+  }
+}
+
 template <typename T>
 __host__ __device__ inline size_t core_fast_smem_bytes(int kmax) {
   const int n = kmax + 1;
-  // V, B (Q2 / S / E), W ((n + 1) x n), Q (n x n), 15 n floats of vectors, 3 n ints, 2 n doubles
-  return (size_t)(4 * n * n + n + 15 * n) * sizeof(float) + (size_t)n * 3 * sizeof(int) + (size_t)n * 2 * sizeof(double) +
+  // V, B (Q2 / S / E), W ((n + 1) x n), Q (n x n), 18 n floats of vectors, 3 n ints, 2 n doubles
+  return (size_t)(4 * n * n + n + 18 * n) * sizeof(float) + (size_t)n * 3 * sizeof(int) + (size_t)n * 2 * sizeof(double) +
          256;
 }
 
@@ -348,8 +423,10 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   float* sig_hi = vec + 6 * n;  // sigma as float pairs (original order)
   float* sig_lo = vec + 7 * n;
   float* u0 = vec + 8 * n;
-  float* sc = vec + 9 * n;      // scalars (>= 4 floats; n >= 1)
-  int* rowmap = reinterpret_cast<int*>(vec + 15 * n);
+  float* sf = vec + 15 * n;   // float sigma
+  float* xf = vec + 16 * n;   // float p (append) or delta * a (entry)
+  float* bf = vec + 17 * n;   // float b (entry)
+  int* rowmap = reinterpret_cast<int*>(vec + 18 * n);
   int* nxt = rowmap + n;
   __shared__ int s_flag;
   __shared__ float s_max[2];
@@ -360,7 +437,11 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     const ff si = ff_of(in.sig[i]);
     sig_hi[i] = si.hi;
     sig_lo[i] = si.lo;
+    sf[i] = si.hi;
+    xf[i] = (float)(in.kind == kEntry ? in.delta * in.a[i] : in.p[i]);
+    bf[i] = in.kind == kEntry ? (float)in.b[i] : 0.f;
   }
+  const float rhof = (float)in.rho;
   bool ok;
   if (in.kind != kEntry) {
     // Ascending poles: (0 for the rho column when grew), sigma_{r-1}^2, ..., sigma_0^2.
@@ -442,10 +523,9 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   // S = W^T W and Q = V^T V (R = I - Q): S into B, Q into the scratch area after W.
   float* Qm = W + (size_t)(n + 1) * n;  // n x n (reuses the tail of the work area)
   for (;; ++pass) {
-    structured_kv(in, nr, n, V, W, tmp);
+    structured_kv(in, nr, n, V, W, tmp, sf, xf, bf, rhof);
     if (t < 2) s_max[t] = 0.f;
-    smem_syrk(n, nr, W, nr, B);
-    smem_syrk(n, n, V, n, Qm);
+    smem_two_syrk(n, nr, W, V, B, Qm);
     __syncthreads();
     float offm = 0.f, rm = 0.f;
     for (int idx = t; idx < n * n; idx += blockDim.x) {
@@ -502,7 +582,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   ISVD_STAMP(4);
   // W = K V is current. Column norms of W, and the singular values ||K v_j|| / ||v_j|| in
   // float-float arithmetic through K's structure (FP64-class accuracy on the FP32 pipes).
-  const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int lane = t & 31, warp = t >> 5;
   double* sref = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(nxt + n) + 15) & ~uintptr_t(15));
   double* nrm = sref + n;
   int* perm = reinterpret_cast<int*>(nrm + n);
@@ -526,7 +606,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   float* acc_lo = vec + 11 * n;
   float* nv_hi = vec + 12 * n;
   float* nv_lo = vec + 13 * n;
-  float* inv_nrm = vec + 14 * n;  // 1 / ||W_j||
+  float* inv_nrm = vec + 14 * n;  // 1 / ||W_j||  (declared again below for the output phase)
   {
     const int g = t & (kSecLanes - 1);
     const int ngr = blockDim.x / kSecLanes;
@@ -609,11 +689,22 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   }
   __syncthreads();
   const int k_out = in.kt < nc ? in.kt : nc;
-  double nmax = 0.0;
-  for (int j = 0; j < n; ++j) nmax = fmax(nmax, nrm[j]);
-  // A kept singular value at the FP32 noise floor has no reliable left vector here.
-  for (int jj = 0; jj < k_out; ++jj)
-    if (!(nrm[perm[jj]] > nmax * 1e-5)) return -1;
+  // A kept singular value at the FP32 noise floor has no reliable left vector here (one warp,
+  // FP32, on the reciprocal norms: small ||W_j|| <=> large 1 / ||W_j||).
+  if (warp == 0) {
+    float mx = 0.f;
+    for (int j = lane; j < n; j += 32) mx = fmaxf(mx, inv_nrm[j] > 0.f ? 1.f / inv_nrm[j] : 0.f);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int bad = 0;
+    for (int jj = lane; jj < k_out; jj += 32) {
+      const float nj = inv_nrm[perm[jj]] > 0.f ? 1.f / inv_nrm[perm[jj]] : 0.f;
+      bad |= !(nj > mx * 1e-5f);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) s_flag = bad;
+  }
+  __syncthreads();
+  if (s_flag) return -1;
   for (int idx = t; idx < nr * k_out; idx += blockDim.x) {
     const int row = idx / k_out, jj = idx - row * k_out;
     const int j = perm[jj];

@@ -66,6 +66,8 @@ struct isvd_ctx {
   void* Rl = nullptr;
   int64_t rl_cap = 0;
   int rsvd_p = 16, rsvd_q = 2;
+  int64_t opt_t = -1;  // t at which Uopt/Vopt/sig_opt hold the truncated SVD of A_t
+  int opt_rank = 0;
   uint64_t seed = 0;
   int64_t rsvd_calls = 0;
   isvd_policy pol{};
@@ -488,11 +490,6 @@ isvd_status sym_eig(isvd_ctx* h, const double* G, int n, double* evals, double* 
 }
 
 
-isvd_status sticky_check(isvd_ctx* h) {
-  if (h->sticky) return (isvd_status)h->sticky;
-  return ISVD_OK;
-}
-
 isvd_status read_state(isvd_ctx* h, DevState* out) {
   CK(h, cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -680,7 +677,14 @@ template <typename T>
 isvd_status do_refresh(isvd_ctx* h, int store) {
   const int kr = (int)std::min<int64_t>(h->k_host, std::min(h->m, h->n));
   isvd_status s;
-  if ((s = tsvd<T>(h, kr, (T*)h->U, h->sig, (T*)h->V))) return s;
+  if (h->opt_t == h->t && h->opt_rank == kr && h->Uopt && h->Vopt) {
+    // The policy check at this same t already computed TruncatedSVD(A_t, kr) for its metrics.
+    CK(h, cudaMemcpyAsync(h->U, h->Uopt, (size_t)h->m * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->V, h->Vopt, (size_t)h->n * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->sig, h->sig_opt, (size_t)kr * 8, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    if ((s = tsvd<T>(h, kr, (T*)h->U, h->sig, (T*)h->V))) return s;
+  }
   if ((s = set_rank<T>(h, kr))) return s;
   if (store && (s = store_ref<T>(h, kr))) return s;
   h->t_last = h->t;
@@ -762,6 +766,8 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   if ((s = ensure_buf(h, &h->Uopt, &h->uopt_cap, h->m * h->ld * (int64_t)h->es))) return s;
   if ((s = ensure_buf(h, &h->Vopt, &h->vopt_cap, h->n * h->ld * (int64_t)h->es))) return s;
   if ((s = tsvd<T>(h, r, (T*)h->Uopt, h->sig_opt, (T*)h->Vopt))) return s;
+  h->opt_t = h->t;
+  h->opt_rank = r;
   double sc[2];
   CK(h, cudaMemcpyAsync(sc, h->scal, 16, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
