@@ -226,6 +226,62 @@ isvd_status isvd_latencies(isvd_t h, double* us, int64_t cap, int64_t* count);
 const char* isvd_last_error(isvd_t h);
 const char* isvd_status_string(isvd_status s);
 
+/* --- batched pool of independent streams ---------------------------------------------------
+ * Many streams (each the single-stream engine above, FP32 bulk) share one CUDA stream. A submit
+ * takes an ordered list of ops; ops of the same stream are applied in list order, ops of different
+ * streams are grouped into "ticks" (at most one op per stream) and each tick is ONE fused kernel
+ * launch in which one CTA performs one whole update (projection, core SVD, rotations, dense-A and
+ * N_t bookkeeping) of one stream. Streams are admitted under an HBM budget. The pool path runs no
+ * refresh policy; isvd_pool_stream gives the stream's handle for refresh, metrics and reads. */
+typedef struct isvd_pool_ctx* isvd_pool_t;
+
+typedef struct {
+  int32_t k_max;             /* rank capacity of every stream, 1..64 */
+  int32_t reserved;
+  int64_t max_streams;       /* slot limit (0: unlimited) */
+  int64_t hbm_budget_bytes;  /* admission budget for the streams' device memory (0: unlimited) */
+  void* cuda_stream;         /* CUDA stream of all pool work (NULL: legacy default stream) */
+  double tol_rel;            /* rank test (<= 0: 3e-6) */
+} isvd_pool_config;
+
+/* One op of a pool submit: kind 0 row append, 1 column append, 2 entry update (as isvd_event). */
+typedef struct {
+  int32_t stream;
+  int32_t kind;
+  int64_t i, j;
+  double delta;
+  int64_t off, len;  /* FP32 payload slice for appends */
+} isvd_op;
+
+isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out);
+void isvd_pool_destroy(isvd_pool_t p);
+
+/* Admits a stream started from A0 (FP32, m0 x n0, row stride lda) at rank k <= k_max, with
+ * initial capacities row_cap/col_cap, optionally from given factors (U0, sigma0, V0 as in
+ * isvd_create_from_factors; NULL to compute TruncatedSVD(A0, k)). Returns ISVD_EBUDGET (nothing
+ * admitted) when the stream's device footprint would exceed the budget or the slots are full. */
+isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n0, int64_t lda, int k,
+                            int64_t row_cap, int64_t col_cap, const void* U0, const double* sigma0,
+                            const void* V0, int on_device, int32_t* stream_id);
+
+/* Releases a stream and its memory (synchronises). */
+isvd_status isvd_pool_release(isvd_pool_t p, int32_t stream_id);
+
+/* Queues ops (see above). All ops are validated (shape, bounds, finiteness) before any work is
+ * queued; on error nothing is queued. payload is FP32, host or device memory. */
+isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, const void* payload,
+                             int64_t payload_len, int payload_on_device);
+
+/* Waits for the pool's work; reports sticky device errors of any stream. */
+isvd_status isvd_pool_sync(isvd_pool_t p);
+
+/* The single-stream handle of a pool stream (owned by the pool; do not destroy), or NULL. */
+isvd_t isvd_pool_stream(isvd_pool_t p, int32_t stream_id);
+
+int64_t isvd_pool_bytes_used(isvd_pool_t p);
+int64_t isvd_pool_kernel_launches(isvd_pool_t p);
+const char* isvd_pool_last_error(isvd_pool_t p);
+
 /* --- allocation-free orthogonality measurement ----------------------------------------------
  * The paper has no counterpart: this is a library service for callers that cannot allocate
  * device memory, e.g. code running under a memory pool that forbids new allocations, code that

@@ -60,6 +60,16 @@ class Metrics(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PoolConfig(C.Structure):
+    _fields_ = [("k_max", C.c_int32), ("reserved", C.c_int32), ("max_streams", C.c_int64),
+                ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double)]
+
+
+class PoolOp(C.Structure):
+    _fields_ = [("stream", C.c_int32), ("kind", C.c_int32), ("i", C.c_int64), ("j", C.c_int64),
+                ("delta", C.c_double), ("off", C.c_int64), ("len", C.c_int64)]
+
+
 class Event(C.Structure):
     _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("i", C.c_int64), ("j", C.c_int64),
                 ("delta", C.c_double), ("off", C.c_int64), ("len", C.c_int64)]
@@ -95,6 +105,17 @@ _SIGS = {
     "isvd_latencies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "isvd_last_error": (C.c_char_p, [C.c_void_p]),
     "isvd_status_string": (C.c_char_p, [C.c_int]),
+    "isvd_pool_create": (C.c_int, [C.POINTER(PoolConfig), C.POINTER(C.c_void_p)]),
+    "isvd_pool_destroy": (None, [C.c_void_p]),
+    "isvd_pool_admit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int64,
+                                  C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]),
+    "isvd_pool_release": (C.c_int, [C.c_void_p, C.c_int32]),
+    "isvd_pool_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int]),
+    "isvd_pool_sync": (C.c_int, [C.c_void_p]),
+    "isvd_pool_stream": (C.c_void_p, [C.c_void_p, C.c_int32]),
+    "isvd_pool_bytes_used": (C.c_int64, [C.c_void_p]),
+    "isvd_pool_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "isvd_pool_last_error": (C.c_char_p, [C.c_void_p]),
 }
 
 
@@ -289,3 +310,93 @@ class ISVD:
 
     def __exit__(self, *a):
         self.close()
+
+
+class _Borrowed(ISVD):
+    """A pool stream's handle (owned by the pool)."""
+
+    def __init__(self, handle, dtype=np.float32):
+        self.prec = FP32
+        self.dtype = dtype
+        self._h = C.c_void_p(handle)
+
+    def close(self):
+        self._h = None
+
+
+class Pool:
+    """Many independent FP32 streams updated by fused per-tick launches (isvd_pool_*)."""
+
+    def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0):
+        cfg = PoolConfig(k_max=k_max, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
+                         cuda_stream=stream or 0, tol_rel=tol_rel)
+        h = C.c_void_p()
+        st = lib().isvd_pool_create(C.byref(cfg), C.byref(h))
+        if st:
+            raise IsvdError(st, "isvd_pool_create")
+        self._p = h
+
+    def _check(self, st, what):
+        if st:
+            raise IsvdError(st, f"{what}: {lib().isvd_pool_last_error(self._p).decode()}")
+
+    def admit(self, A0, k, row_cap=0, col_cap=0, factors=None):
+        A0 = np.ascontiguousarray(A0, dtype=np.float32)
+        m0, n0 = A0.shape
+        sid = C.c_int32()
+        if factors is None:
+            st = lib().isvd_pool_admit(self._p, A0.ctypes.data, m0, n0, n0, int(k), row_cap, col_cap, None, None,
+                                       None, 0, C.byref(sid))
+        else:
+            U0 = np.ascontiguousarray(factors[0], dtype=np.float32)
+            s0 = np.ascontiguousarray(factors[1], dtype=np.float64)
+            V0 = np.ascontiguousarray(factors[2], dtype=np.float32)
+            st = lib().isvd_pool_admit(self._p, A0.ctypes.data, m0, n0, n0, int(k), row_cap, col_cap, U0.ctypes.data,
+                                       s0.ctypes.data, V0.ctypes.data, 0, C.byref(sid))
+        self._check(st, "isvd_pool_admit")
+        return sid.value
+
+    def release(self, sid):
+        self._check(lib().isvd_pool_release(self._p, int(sid)), "isvd_pool_release")
+
+    def submit(self, ops, payload):
+        """ops: structured array / list of (stream, kind, i, j, delta, off, len); payload: FP32."""
+        n = len(ops)
+        arr = (PoolOp * max(n, 1))()
+        for e, o in enumerate(ops):
+            arr[e].stream, arr[e].kind, arr[e].i, arr[e].j, arr[e].delta, arr[e].off, arr[e].len = o
+        if isinstance(payload, np.ndarray):
+            payload = np.ascontiguousarray(payload, dtype=np.float32)
+        p, d = _ptr(payload)
+        self._check(lib().isvd_pool_submit(self._p, arr, n, p, payload.shape[0], d), "isvd_pool_submit")
+
+    def submit_raw(self, arr, n, payload_ptr, payload_len, on_device):
+        self._check(lib().isvd_pool_submit(self._p, arr, n, payload_ptr, payload_len, on_device), "isvd_pool_submit")
+
+    def sync(self):
+        self._check(lib().isvd_pool_sync(self._p), "isvd_pool_sync")
+
+    def stream(self, sid):
+        h = lib().isvd_pool_stream(self._p, int(sid))
+        if not h:
+            raise IsvdError(1, "no such stream")
+        return _Borrowed(h)
+
+    @property
+    def bytes_used(self):
+        return int(lib().isvd_pool_bytes_used(self._p))
+
+    @property
+    def launches(self):
+        return int(lib().isvd_pool_kernel_launches(self._p))
+
+    def close(self):
+        if self._p:
+            lib().isvd_pool_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/isvd.h"
+#include "pool_kernels.cuh"
 #include "refresh_kernels.cuh"
 #include "update_kernels.cuh"
 
@@ -1248,5 +1249,330 @@ isvd_status isvd_latencies(isvd_t h, double* us, int64_t cap, int64_t* count) {
 }
 
 const char* isvd_last_error(isvd_t h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"
+
+// ---- batched pool of streams ----------------------------------------------------------------
+
+struct isvd_pool_ctx {
+  int kmax = 32, kb = 32;
+  cudaStream_t stream = nullptr;
+  int64_t budget = 0, used = 0, max_streams = 0;
+  double tol_rel = 3e-6;
+  isvd_config cfg{};
+  std::vector<isvd_ctx*> streams;
+  std::vector<int64_t> bytes;
+  PoolOp* ops_dev = nullptr;
+  int64_t ops_cap = 0;
+  PoolOp* ops_pinned = nullptr;
+  int64_t pinned_cap = 0;
+  void* payload = nullptr;
+  int64_t payload_cap = 0;
+  cudaEvent_t copied = nullptr;
+  int64_t launches = 0, ticks = 0, fused_ops = 0, fallback_ops = 0;
+  std::string err;
+};
+
+namespace {
+
+isvd_status pool_fail(isvd_pool_ctx* p, isvd_status s, const std::string& m) {
+  p->err = m;
+  return s;
+}
+
+template <int KB>
+isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
+  k_pool_tick<KB><<<count, pool_threads(KB), pool_smem_bytes<KB>(), p->stream>>>(ops);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool tick launch: ") + cudaGetErrorString(e));
+  p->launches++;
+  return ISVD_OK;
+}
+
+int64_t stream_footprint(int64_t row_cap, int64_t col_cap, int ld) {
+  // U, V, U_ref and A in FP32 plus the handle's fixed workspace.
+  const int64_t fixed = (int64_t)6 * (kKmaxLimit + 1) * (kKmaxLimit + 1) * 8 + (int64_t)kMaxProjBlocks * kPartStride * 8 +
+                        (int64_t)4 * (kKmaxLimit + 2) * ld * 4;
+  return (2 * row_cap * ld + col_cap * ld + row_cap * col_cap) * 4 + fixed;
+}
+
+}  // namespace
+
+extern "C" {
+
+isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
+  if (!cfg || !out) return ISVD_EINVAL;
+  *out = nullptr;
+  if (cfg->k_max < 1 || cfg->k_max > 64) return ISVD_EINVAL;
+  isvd_pool_ctx* p = new isvd_pool_ctx();
+  p->kmax = cfg->k_max;
+  p->kb = kb_bucket(cfg->k_max);
+  p->stream = (cudaStream_t)cfg->cuda_stream;
+  p->budget = cfg->hbm_budget_bytes;
+  p->max_streams = cfg->max_streams > 0 ? cfg->max_streams : (int64_t)1 << 30;
+  p->tol_rel = cfg->tol_rel > 0 ? cfg->tol_rel : 3e-6;
+  p->cfg.prec = ISVD_FP32;
+  p->cfg.k_max = p->kmax;
+  p->cfg.tol_rel = p->tol_rel;
+  p->cfg.cuda_stream = cfg->cuda_stream;
+  p->cfg.orth_every = (int64_t)1 << 62;  // the pool path runs no monitor; isvd_reorthogonalize on demand
+  p->cfg.rsvd_power_iters = -1;
+  cudaError_t e = cudaSuccess;
+  switch (p->kb) {
+    case 16: e = cudaFuncSetAttribute(k_pool_tick<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<16>()); break;
+    case 32: e = cudaFuncSetAttribute(k_pool_tick<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>()); break;
+    default: e = cudaFuncSetAttribute(k_pool_tick<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<64>()); break;
+  }
+  if (e != cudaSuccess || cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming) != cudaSuccess) {
+    delete p;
+    return ISVD_ECUDA;
+  }
+  *out = p;
+  return ISVD_OK;
+}
+
+void isvd_pool_destroy(isvd_pool_t p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  for (isvd_ctx* h : p->streams)
+    if (h) isvd_destroy(h);
+  if (p->ops_dev) cudaFree(p->ops_dev);
+  if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
+  if (p->payload) cudaFree(p->payload);
+  if (p->copied) cudaEventDestroy(p->copied);
+  delete p;
+}
+
+isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n0, int64_t lda, int k,
+                            int64_t row_cap, int64_t col_cap, const void* U0, const double* sigma0, const void* V0,
+                            int on_device, int32_t* stream_id) {
+  if (!p || !A0 || !stream_id || k < 1 || k > p->kmax) return ISVD_EINVAL;
+  int64_t live = 0;
+  for (isvd_ctx* h : p->streams) live += h != nullptr;
+  if (live >= p->max_streams) return pool_fail(p, ISVD_EBUDGET, "pool: stream slots exhausted");
+  isvd_config c = p->cfg;
+  c.row_cap = std::max<int64_t>(row_cap, m0 + 1);
+  c.col_cap = std::max<int64_t>(col_cap, n0 + 1);
+  const int64_t need = stream_footprint(c.row_cap, c.col_cap, round_up(p->kmax, 4));
+  if (p->budget > 0 && p->used + need > p->budget)
+    return pool_fail(p, ISVD_EBUDGET, "pool: HBM budget exceeded (" + std::to_string(p->used + need) + " > " +
+                                          std::to_string(p->budget) + " bytes)");
+  isvd_t h = nullptr;
+  const int r0 = (int)std::min<int64_t>(k, std::min(m0, n0));
+  isvd_status s = U0 ? isvd_create_from_factors(&c, A0, m0, n0, lda, U0, sigma0, V0, r0, k, on_device, &h)
+                     : isvd_create(&c, A0, m0, n0, lda, k, on_device, &h);
+  if (s) return s;
+  int32_t id = -1;
+  for (size_t i = 0; i < p->streams.size(); ++i)
+    if (!p->streams[i]) {
+      id = (int32_t)i;
+      break;
+    }
+  if (id < 0) {
+    id = (int32_t)p->streams.size();
+    p->streams.push_back(nullptr);
+    p->bytes.push_back(0);
+  }
+  p->streams[id] = h;
+  p->bytes[id] = need;
+  p->used += need;
+  *stream_id = id;
+  return ISVD_OK;
+}
+
+isvd_status isvd_pool_release(isvd_pool_t p, int32_t sid) {
+  if (!p || sid < 0 || sid >= (int32_t)p->streams.size() || !p->streams[sid]) return ISVD_EINVAL;
+  cudaStreamSynchronize(p->stream);
+  isvd_destroy(p->streams[sid]);
+  p->streams[sid] = nullptr;
+  p->used -= p->bytes[sid];
+  p->bytes[sid] = 0;
+  return ISVD_OK;
+}
+
+isvd_t isvd_pool_stream(isvd_pool_t p, int32_t sid) {
+  if (!p || sid < 0 || sid >= (int32_t)p->streams.size()) return nullptr;
+  return p->streams[sid];
+}
+
+int64_t isvd_pool_bytes_used(isvd_pool_t p) { return p ? p->used : 0; }
+
+int64_t isvd_pool_kernel_launches(isvd_pool_t p) { return p ? p->launches : 0; }
+
+isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, const void* payload,
+                             int64_t payload_len, int payload_on_device) {
+  if (!p || (nops > 0 && !ops)) return ISVD_EINVAL;
+  if (nops == 0) return ISVD_OK;
+  const size_t es = 4;
+  // Validate every op against the shapes it will see (per-stream order), before any work.
+  std::vector<int64_t> mm(p->streams.size()), nn(p->streams.size());
+  std::vector<int32_t> seen(p->streams.size(), 0);
+  std::vector<int32_t> tick_of(nops);
+  int32_t nticks = 0;
+  for (size_t s_ = 0; s_ < p->streams.size(); ++s_)
+    if (p->streams[s_]) {
+      mm[s_] = p->streams[s_]->m;
+      nn[s_] = p->streams[s_]->n;
+      if (p->streams[s_]->sticky) return (isvd_status)p->streams[s_]->sticky;
+    }
+  for (int64_t e = 0; e < nops; ++e) {
+    const isvd_op& o = ops[e];
+    if (o.stream < 0 || o.stream >= (int32_t)p->streams.size() || !p->streams[o.stream])
+      return pool_fail(p, ISVD_EINVAL, "pool op " + std::to_string(e) + ": unknown stream");
+    const int32_t sid = o.stream;
+    if (o.kind == kEntry) {
+      if (o.i < 0 || o.i >= mm[sid] || o.j < 0 || o.j >= nn[sid] || !std::isfinite(o.delta))
+        return pool_fail(p, ISVD_EBOUNDS, "pool op " + std::to_string(e) + ": entry out of range");
+    } else if (o.kind == kRow || o.kind == kCol) {
+      const int64_t want = o.kind == kRow ? nn[sid] : mm[sid];
+      if (o.len != want) return pool_fail(p, ISVD_ESHAPE, "pool op " + std::to_string(e) + ": length mismatch");
+      if (o.off < 0 || o.off + o.len > payload_len) return pool_fail(p, ISVD_EBOUNDS, "pool op payload out of range");
+      if (o.kind == kRow) mm[sid]++;
+      else nn[sid]++;
+    } else {
+      return pool_fail(p, ISVD_EINVAL, "pool op: unknown kind");
+    }
+    tick_of[e] = seen[sid]++;
+    nticks = std::max(nticks, tick_of[e] + 1);
+  }
+  if (!payload_on_device && payload_len > 0 &&
+      !host_finite((const float*)payload, payload_len))
+    return pool_fail(p, ISVD_ENONFINITE, "pool payload has non-finite values");
+  const float* pay = (const float*)payload;
+  if (!payload_on_device && payload_len > 0) {
+    if (payload_len * (int64_t)es > p->payload_cap) {
+      cudaStreamSynchronize(p->stream);
+      if (p->payload) cudaFree(p->payload);
+      p->payload = nullptr;
+      p->payload_cap = std::max(payload_len * (int64_t)es, 2 * p->payload_cap);
+      if (cudaMalloc(&p->payload, (size_t)p->payload_cap) != cudaSuccess) {
+        p->payload_cap = 0;
+        return pool_fail(p, ISVD_ENOMEM, "pool payload buffer");
+      }
+    }
+    if (cudaMemcpyAsync(p->payload, payload, (size_t)payload_len * es, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool payload copy");
+    pay = (const float*)p->payload;
+  }
+  // Order ops by tick (stable), build descriptors, then one descriptor copy for all ticks.
+  std::vector<int64_t> order(nops), tick_start(nticks + 1, 0);
+  for (int64_t e = 0; e < nops; ++e) tick_start[tick_of[e] + 1]++;
+  for (int32_t t = 0; t < nticks; ++t) tick_start[t + 1] += tick_start[t];
+  {
+    std::vector<int64_t> fill(tick_start.begin(), tick_start.end() - 1);
+    for (int64_t e = 0; e < nops; ++e) order[fill[tick_of[e]]++] = e;
+  }
+  if (nops > p->pinned_cap) {
+    cudaEventSynchronize(p->copied);
+    if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
+    p->pinned_cap = std::max<int64_t>(nops, 2 * p->pinned_cap);
+    if (cudaMallocHost((void**)&p->ops_pinned, sizeof(PoolOp) * (size_t)p->pinned_cap) != cudaSuccess) {
+      p->pinned_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool pinned descriptors");
+    }
+  }
+  if (nops > p->ops_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->ops_dev) cudaFree(p->ops_dev);
+    p->ops_cap = std::max<int64_t>(nops, 2 * p->ops_cap);
+    if (cudaMalloc((void**)&p->ops_dev, sizeof(PoolOp) * (size_t)p->ops_cap) != cudaSuccess) {
+      p->ops_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool descriptors");
+    }
+  }
+  cudaEventSynchronize(p->copied);  // the previous submit's descriptor copy has finished
+  isvd_status s;
+  // Grow every stream to its final shape for this submit BEFORE building descriptors, so that no
+  // reallocation can invalidate a descriptor or copy data ahead of queued work.
+  for (size_t s_ = 0; s_ < p->streams.size(); ++s_) {
+    isvd_ctx* h = p->streams[s_];
+    if (!h) continue;
+    if ((s = ensure_rows(h, mm[s_] + 1))) return s;
+    if ((s = ensure_cols(h, nn[s_] + 1))) return s;
+  }
+  std::vector<char> fused(nops, 0);
+  for (int32_t t = 0; t < nticks; ++t) {
+    for (int64_t q = tick_start[t]; q < tick_start[t + 1]; ++q) {
+      const int64_t e = order[q];
+      const isvd_op& o = ops[e];
+      isvd_ctx* h = p->streams[o.stream];
+      const int64_t prow = o.kind == kRow ? h->n : h->m;
+      fused[q] = (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
+      PoolOp& d = p->ops_pinned[q];
+      d.U = (float*)h->U;
+      d.V = (float*)h->V;
+      d.A = (float*)h->A;
+      d.st = h->st;
+      d.sig = h->sig;
+      d.x = o.kind == kEntry ? nullptr : pay + o.off;
+      d.m = h->m;
+      d.n = h->n;
+      d.lda = h->col_cap;
+      d.i = o.i;
+      d.j = o.j;
+      d.delta = o.delta;
+      d.tol_rel = h->tol_rel;
+      d.ld = h->ld;
+      d.kind = o.kind;
+      if (o.kind == kRow) h->m += 1;
+      else if (o.kind == kCol) h->n += 1;
+      h->t += 1;
+    }
+  }
+  if (cudaMemcpyAsync(p->ops_dev, p->ops_pinned, sizeof(PoolOp) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
+      cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool descriptor copy");
+  cudaEventRecord(p->copied, p->stream);
+  for (int32_t t = 0; t < nticks; ++t) {
+    // Fused ops of the tick are contiguous runs; ops outside the fused kernel's limits take the
+    // single-stream kernels, in the same stream order.
+    int64_t q = tick_start[t];
+    while (q < tick_start[t + 1]) {
+      int64_t q2 = q;
+      while (q2 < tick_start[t + 1] && fused[q2] == fused[q]) ++q2;
+      if (fused[q]) {
+        const int cnt = (int)(q2 - q);
+        switch (p->kb) {
+          case 16: s = pool_launch<16>(p, p->ops_dev + q, cnt); break;
+          case 32: s = pool_launch<32>(p, p->ops_dev + q, cnt); break;
+          default: s = pool_launch<64>(p, p->ops_dev + q, cnt); break;
+        }
+        if (s) return s;
+        p->fused_ops += cnt;
+      } else {
+        for (int64_t z = q; z < q2; ++z) {
+          const PoolOp& d = p->ops_pinned[z];
+          isvd_ctx* h = p->streams[ops[order[z]].stream];
+          // Replay the shape the op saw, run the single-stream path, restore the advanced shape.
+          const int64_t m_after = h->m, n_after = h->n;
+          h->m = d.m;
+          h->n = d.n;
+          s = do_append<float>(h, d.kind, d.x);
+          h->m = m_after;
+          h->n = n_after;
+          if (s) return s;
+          p->fallback_ops++;
+        }
+      }
+      q = q2;
+    }
+    p->ticks++;
+  }
+  return ISVD_OK;
+}
+
+isvd_status isvd_pool_sync(isvd_pool_t p) {
+  if (!p) return ISVD_EINVAL;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool sync");
+  for (isvd_ctx* h : p->streams) {
+    if (!h) continue;
+    DevState ds;
+    isvd_status s = read_state(h, &ds);
+    if (s) return s;
+  }
+  return ISVD_OK;
+}
+
+const char* isvd_pool_last_error(isvd_pool_t p) { return p ? p->err.c_str() : "null pool"; }
 
 }  // extern "C"
