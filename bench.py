@@ -1,7 +1,13 @@
 #!/usr/bin/env python
-"""Throughput and latency of the incremental-SVD update stream on one GB300 (or N replicas).
+"""Throughput and latency of incremental-SVD updates on one GB300 (or N replicas).
 
-Workload (default): one FP32-bulk stream started from a 2,000 x 1,000 factor-model panel
+Default workload ``batched-4096``: 4,096 independent FP32-bulk streams, each a factor-model panel
+(n ~ U[50, 500] assets, m0 = 2n rows, 5 factors, Student-t noise, k ~ {8, 16, 32}); one step = one
+tick = one row append on every stream through the pool's fused launch, compared with the plain GPU
+form (the same streams driven through the per-stream single-stream kernels, one launch sequence
+per stream update). Error ratios of a sample of streams are measured after the timed region.
+
+Workload ``panel-2000x1000-k64``: one FP32-bulk stream started from a 2,000 x 1,000 factor-model panel
 (20 factors, Student-t noise), k = 64, mixed updates 70% row appends / 10% column appends /
 20% rank-1 entry updates (delta sd 0.005), error-threshold refresh (ratio > 1.05) and
 angle-threshold refresh (largest principal angle to the optimal subspace > 5 degrees) checked
@@ -110,6 +116,22 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device="cuda") -> float:
+    """Max over ranks of a per-rank float (the timed region's duration), identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Replica r runs its own seeded stream(s); ranks never share inputs."""
+    return 1000 + 7919 * rank
+
+
 def make_stream(name, seed, n_events):
     A0, ev, k, extra = streams.workload(name, seed=seed, n_events=n_events)
     return A0, ev, k
@@ -131,7 +153,7 @@ def run_gb300(args):
     B = args.batch or W["batch"]
     K, Wm = args.steps, args.warmup
     n_ev = (Wm + 2 * K) * B
-    A0, ev, k = make_stream(args.workload, seed=rank, n_events=n_ev)
+    A0, ev, k = make_stream(args.workload, seed=rank_seed(rank), n_events=n_ev)
     prec = pkg.FP32 if W["prec"] == "fp32" else pkg.FP64
     dt = np.float32 if prec == pkg.FP32 else np.float64
     st = torch.cuda.Stream()
@@ -166,6 +188,7 @@ def run_gb300(args):
     ratios = []
     clocks.start()
     evs = []
+    torch.cuda.nvtx.range_push("timed")
     for i in range(Wm, Wm + K):
         flush.zero_()                       # evict L2 (129 MB) between steps, outside the timing
         st.wait_stream(torch.cuda.current_stream())
@@ -176,16 +199,14 @@ def run_gb300(args):
         evs.append((e0, e1))
         ratios.append(g.last_check_metrics()["frob_ratio"])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = g.launches - l0
     ms = sum(a.elapsed_time(b_) for a, b_ in evs)
     prof = g.profile_read()
     lat = g.latencies_us()
     g.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, world)
     value = world * K * B / (ms / 1e3)
 
     # End to end through the public API with host buffers: each step copies its payload from
@@ -211,11 +232,7 @@ def run_gb300(args):
             h2d += pinned[j].numel() * pinned[j].element_size() + 48 * len(sl)
             d2h += sig.nbytes
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = reduce_max(time.perf_counter() - t0, world)
         e2e = {"value": world * K * B / el, "unit": "updates/s", "h2d_bytes_per_step": int(h2d // K),
                "d2h_bytes_per_step": int(d2h // K)}
 
@@ -289,7 +306,7 @@ def run_batched(args):
     K, Wm = args.steps, args.warmup
     plain_ticks = args.plain_ticks
     T = Wm + K + plain_ticks + (K if not args.no_e2e else 0)
-    rng = np.random.Generator(np.random.PCG64(1000 + rank))
+    rng = np.random.Generator(np.random.PCG64(rank_seed(rank)))
     ns = rng.integers(W["n_lo"], W["n_hi"] + 1, size=S)
     ks = rng.choice(np.asarray(W["ks"]), size=S)
     st = torch.cuda.Stream()
@@ -298,7 +315,7 @@ def run_batched(args):
     ids, rows, payload_parts, offs = [], [], [], []
     for sidx in range(S):
         n = int(ns[sidx])
-        A0, fm = streams.make_panel(2 * n, n, 5, seed=rank * 1_000_003 + sidx + 1)
+        A0, fm = streams.make_panel(2 * n, n, 5, seed=rank_seed(rank) * 1_000_003 + sidx + 1)
         ids.append(pool.admit(A0.astype(np.float32), int(ks[sidx]), row_cap=2 * n + T + 8, col_cap=n + 2))
         rows.append(fm.rows(T).astype(np.float32))
     setup_s = time.perf_counter() - t0
@@ -335,25 +352,26 @@ def run_batched(args):
     clocks = Clocks(local)
     l0 = pool.launches
     clocks.start()
-    evs, tick_bytes = [], []
+    evs, tick_bytes, host_s = [], [], []
+    torch.cuda.nvtx.range_push("timed")
     for t in range(Wm, Wm + K):
         m_now = 2 * ns + t
         tick_bytes.append(float(np.sum((2.0 * (m_now + ns) * ks + 2.0 * ns) * 4)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
+        h0 = time.perf_counter()
         tick_dev(t)
+        host_s.append(time.perf_counter() - h0)
         e1.record(st)
         evs.append((e0, e1))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = pool.launches - l0
     tick_ms = np.array([a.elapsed_time(b_) for a, b_ in evs])
     ms = float(tick_ms.sum())
     pool.sync()
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(ms, world)
     value = world * K * S / (ms / 1e3)
     # Plain GPU form: the same streams, next ticks, one single-stream launch sequence per stream.
     handles = [pool.stream(i) for i in ids]
@@ -362,6 +380,7 @@ def run_batched(args):
     pe0 = torch.cuda.Event(enable_timing=True)
     pe1 = torch.cuda.Event(enable_timing=True)
     pe0.record(st)
+    torch.cuda.nvtx.range_push("plain")
     for t in range(Wm + K, Wm + K + plain_ticks):
         base = t * tick_len
         for sidx in range(S):
@@ -370,7 +389,8 @@ def run_batched(args):
             handles[sidx].append_row(x)
     pe1.record(st)
     torch.cuda.synchronize()
-    plain_value = plain_ticks * S / (pe0.elapsed_time(pe1) / 1e3)
+    torch.cuda.nvtx.range_pop()
+    plain_value = plain_ticks * S / (pe0.elapsed_time(pe1) / 1e3) if plain_ticks > 0 else None
     e2e = None
     if not args.no_e2e:
         base_t = Wm + K + plain_ticks
@@ -385,9 +405,16 @@ def run_batched(args):
             sig = handles[0].sigma()
             d2h += sig.nbytes
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = reduce_max(time.perf_counter() - t0, world)
         e2e = {"value": world * K * S / el, "unit": "updates/s", "h2d_bytes_per_step": int(tick_len * 4 + S * 48),
                "d2h_bytes_per_step": int(d2h // K)}
+    # Accuracy gate: error ratio (Section 2.5) of a sample of streams after the timed ticks.
+    ratios, sweeps = [], []
+    for sidx in range(0, S, max(1, S // 8)):
+        mt = handles[sidx].metrics(full=True)
+        ratios.append(mt["frob_ratio"])
+    for sidx in range(0, S, max(1, S // 256)):
+        sweeps.append(handles[sidx].metrics(full=False)["core_sweeps"])
     if rank != 0:
         return None
     peak, peak_src = measured_peaks()
@@ -399,13 +426,17 @@ def run_batched(args):
         "dtype": "f32", "data": "synthetic (seeded factor-model panels and rows)",
         "config": {"workload": args.workload, "desc": W["desc"], "streams": S, "events_per_step": S,
                    "k_mix": {str(k): int(np.sum(ks == k)) for k in W["ks"]},
-                   "form": "one fused k_pool_tick launch per tick (one CTA per stream update)",
-                   "plain_form_updates_per_s": round(plain_value, 1),
-                   "speedup_vs_plain": round(value / plain_value, 2),
+                   "form": "one fused k_pool_tick launch per rank bucket per tick (one CTA per stream update)",
+                   "plain_form_updates_per_s": round(plain_value, 1) if plain_value else None,
+                   "speedup_vs_plain": round(value / plain_value, 2) if plain_value else None,
                    "l2": "working set per tick larger than L2 (no flush needed)",
                    "latency_us": {"p50": round(float(np.percentile(tick_ms, 50)) * 1e3, 1),
                                   "p99": round(float(np.percentile(tick_ms, 99)) * 1e3, 1),
                                   "note": "an update completes with its tick"},
+                   "err_ratio_sample_max": round(float(np.nanmax(ratios)), 5) if ratios else None,
+                   "host_submit_us_per_tick": round(float(np.mean(host_s)) * 1e6, 1),
+                   "core_fast_path_frac": round(float(np.mean(np.asarray(sweeps) >= 100)), 4) if sweeps else None,
+                   "core_corrected_weights_frac": round(float(np.mean(np.asarray(sweeps) == 102)), 4) if sweeps else None,
                    "setup_s": round(setup_s, 1), "parallelism": "replicas" if world > 1 else "streams in one pool"},
         "roofline": {"kernel": "k_pool_tick", "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4), "traffic": None,
@@ -415,7 +446,46 @@ def run_batched(args):
         "e2e": e2e,
     }
     pool.close()
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline_batched(args, budget_s=args.cpu_budget)
     return out
+
+
+def _batched_sample(args, n_streams, ticks):
+    """Streams of the batched workload for the CPU oracle (same generator, same seeds)."""
+    W = WORKLOADS["batched-4096"]
+    rng = np.random.Generator(np.random.PCG64(rank_seed(0)))
+    S = args.streams or W["streams"]
+    ns = rng.integers(W["n_lo"], W["n_hi"] + 1, size=S)
+    ks = rng.choice(np.asarray(W["ks"]), size=S)
+    out = []
+    for sidx in range(min(n_streams, S)):
+        n = int(ns[sidx])
+        A0, fm = streams.make_panel(2 * n, n, 5, seed=rank_seed(0) * 1_000_003 + sidx + 1)
+        out.append((A0.astype(np.float32).astype(np.float64), fm.rows(ticks).astype(np.float32).astype(np.float64),
+                    int(ks[sidx])))
+    return out
+
+
+def cpu_baseline_batched(args, budget_s=15.0):
+    """The oracle on a time-bounded sample of the batched workload: ticks over the first streams."""
+    import oracle
+    data = _batched_sample(args, 64, 8)
+    engines = [oracle.OracleISVD(A0, k, tol_rel=3e-6) for A0, _, k in data]
+    t0 = time.perf_counter()
+    n = 0
+    for t in range(8):
+        for (A0, rows, k), o in zip(data, engines):
+            o.append_row(rows[t])
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(n / el, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{n} row appends over the first {len(data)} streams of the same workload "
+                      f"(tick order, time budget {budget_s:.0f} s)"}
 
 
 def oracle_policy(W):
@@ -466,6 +536,30 @@ def run_reference(args):
         return None
     import oracle
     W = WORKLOADS[args.workload]
+    if args.workload.startswith("batched"):
+        nst = args.ref_batch
+        data = _batched_sample(args, nst, args.warmup + args.steps)
+        engines = [oracle.OracleISVD(A0, k, tol_rel=3e-6) for A0, _, k in data]
+        for t in range(args.warmup):
+            for (A0, rows, k), o in zip(data, engines):
+                o.append_row(rows[t])
+        t0 = time.perf_counter()
+        for t in range(args.warmup, args.warmup + args.steps):
+            for (A0, rows, k), o in zip(data, engines):
+                o.append_row(rows[t])
+        el = time.perf_counter() - t0
+        value = args.steps * len(data) / el
+        sample = f"{len(data)} streams of the same workload per step (one row append each), {args.steps} steps"
+        return {"impl": "reference", "metric": "iSVD updates/s and p50/p99 update latency at err ratio<=1.05 vs plain GPU form",
+                "value": round(value, 3), "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded factor-model panels and rows)",
+                "config": {"workload": args.workload, "desc": W["desc"], "events_per_step": len(data)},
+                "cpu_baseline": {"value": round(value, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": round(value, 3), "unit": "updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     Bref = args.ref_batch
     n_ev = (args.warmup + args.steps) * Bref
     A0, ev, k = make_stream(args.workload, seed=0, n_events=n_ev)
@@ -506,7 +600,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="panel-2000x1000-k64", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="batched-4096", choices=list(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--ref-batch", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

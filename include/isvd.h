@@ -112,7 +112,8 @@ typedef struct {
   int64_t refreshes;     /* refreshes performed */
   int64_t reorths;       /* re-orthogonalisations performed */
   int64_t t_last;        /* time of the last refresh */
-  int32_t core_sweeps;   /* Jacobi sweeps of the last core SVD (-1: not converged) */
+  int32_t core_sweeps;   /* last core SVD: Jacobi sweeps (-1: not converged), or 100 + i for the secular
+                            core (i = 0, 1: Gram-verified after i refinements; 2: corrected weights) */
   int32_t reserved0;
 } isvd_metrics_t;
 
@@ -257,8 +258,9 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out);
 void isvd_pool_destroy(isvd_pool_t p);
 
 /* Admits a stream started from A0 (FP32, m0 x n0, row stride lda) at rank k <= k_max, with
- * initial capacities row_cap/col_cap, optionally from given factors (U0, sigma0, V0 as in
- * isvd_create_from_factors; NULL to compute TruncatedSVD(A0, k)). Returns ISVD_EBUDGET (nothing
+ * initial capacities row_cap/col_cap, optionally from given factors (U0 m0 x r0, sigma0 r0, V0
+ * n0 x r0, row-major, with r0 = min(k, m0, n0) as in isvd_create_from_factors; the library reads
+ * exactly that many values) or NULL to compute TruncatedSVD(A0, k). Returns ISVD_EBUDGET (nothing
  * admitted) when the stream's device footprint would exceed the budget or the slots are full. */
 isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n0, int64_t lda, int k,
                             int64_t row_cap, int64_t col_cap, const void* U0, const double* sigma0,

@@ -351,6 +351,9 @@ class Pool:
             U0 = np.ascontiguousarray(factors[0], dtype=np.float32)
             s0 = np.ascontiguousarray(factors[1], dtype=np.float64)
             V0 = np.ascontiguousarray(factors[2], dtype=np.float32)
+            r0 = min(int(k), m0, n0)
+            if U0.shape != (m0, r0) or s0.shape != (r0,) or V0.shape != (n0, r0):
+                raise ValueError(f"factors must be ({m0}, {r0}), ({r0},), ({n0}, {r0}) for k = {k}")
             st = lib().isvd_pool_admit(self._p, A0.ctypes.data, m0, n0, n0, int(k), row_cap, col_cap, U0.ctypes.data,
                                        s0.ctypes.data, V0.ctypes.data, 0, C.byref(sid))
         self._check(st, "isvd_pool_admit")

@@ -21,6 +21,14 @@
 namespace isvd {
 
 constexpr int kSecLanes = 8;  // lanes per root
+// Two non-deflated poles closer than kTieRel * (largest pole) count as tied (the CTA Jacobi core
+// takes the update). The poles are float pairs (relative precision ~1e-14) and every difference is
+// formed from them, so gaps well below FP32 resolution still give accurate roots and weights.
+constexpr float kTieRel = 1e-12f;
+// Largest accepted |w_hat_i - w_i| of the corrected weights, in units of eps ||w||: the product
+// for w_hat_i^2 has ~2 n roundings (a random walk of ~4 sqrt(n) eps for n <= 65), so 32 eps
+// rejects only inaccurate roots while keeping the backward error at the FP32 level.
+constexpr float kGeTolEps = 32.f;
 
 // Float-float ("double-FP32") helpers: error-free transformations give FP64-class accuracy on
 // the FP32 pipes, which on this part run ~57x faster than FP64.
@@ -74,9 +82,13 @@ __device__ __forceinline__ ff ff_group_sum(ff v) {
 // entry s. On exit column j of V (column-major, stride ldv) is the unit eigenvector of the j-th
 // smallest eigenvalue, stored as (lam_hi[j] + lam_lo[j]). Returns false (on all threads) when two
 // non-deflated poles coincide to within the FP32 resolution or the order is violated.
+// With tau_out set, the vectors are not formed; instead each root is returned as its origin pole
+// org_out[j] and the offset tau_out[j] from it (lambda_j = d[org_out[j]] + tau_out[j]), for the
+// corrected-weight construction below.
 template <int kTerms>
 __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const float* w, const int* row, float* V,
-                            int ldv, float* lam_hi, float* lam_lo, int* nxt, float* sc, int* s_flag) {
+                            int ldv, float* lam_hi, float* lam_lo, int* nxt, float* sc, int* s_flag,
+                            float* tau_out = nullptr, int* org_out = nullptr) {
   const int t = threadIdx.x;
   if (t == 0) *s_flag = 0;
   if (t < 32) {
@@ -106,7 +118,7 @@ __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const flo
     nxt[j] = nx;
     if (j + 1 < n && ff_sub_to_f(ff{dhi[j + 1], dlo[j + 1]}, ff{dhi[j], dlo[j]}) < 0.f) atomicOr(s_flag, 1);
     if (fabsf(w[j]) > defl_thr && nx >= 0 &&
-        ff_sub_to_f(ff{dhi[nx], dlo[nx]}, ff{dhi[j], dlo[j]}) <= 1e-6f * dscale)
+        ff_sub_to_f(ff{dhi[nx], dlo[nx]}, ff{dhi[j], dlo[j]}) <= kTieRel * dscale)
       atomicOr(s_flag, 1);
   }
   if (t < 32) {  // sum of the non-deflated squared weights (width of the last interval)
@@ -212,9 +224,18 @@ __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const flo
       }
       if (__all_sync(0xffffffffu, done)) break;
     }
-    a = u;
-    b = u;
-    const float tau = sgn * 0.5f * (a + b);
+    const float tau = sgn * u;
+    if (tau_out) {
+      if (live && g == 0) {
+        const ff org = use_hi ? hi : lo;
+        const ff lam = solve ? ff_add(org, ff{tau, 0.f}) : lo;
+        lam_hi[j] = lam.hi;
+        lam_lo[j] = lam.lo;
+        tau_out[j] = solve ? tau : 0.f;
+        org_out[j] = (solve && use_hi) ? nx : j;
+      }
+      continue;
+    }
     float vq[kTerms];
     float nrm2 = 0.f;
 #pragma unroll
@@ -241,6 +262,99 @@ __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const flo
         lam_lo[j] = lam.lo;
       }
     }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Append core vectors from corrected weights (Gu and Eisenstat 1994/95; the construction LAPACK's
+// divide-and-conquer SVD uses for its broken-arrow matrices). Given the computed roots lambda_j of
+// diag(d) + w w^T (as origin pole + tau), the weights w_hat for which those roots are EXACT
+// eigenvalues follow from Loewner's formula
+//   w_hat_i^2 = prod_j (lambda_j - d_i) / prod_{l != i} (d_l - d_i)   (non-deflated i, j, l),
+// evaluated as a product of ratios, each pairing a root with the pole next to it so that every
+// factor is positive and of moderate size. Every difference lambda_j - d_i is taken as
+// (d_org(j) - d_i) + tau_j from the float-pair poles, so it keeps its relative accuracy. Then
+//   v_j = (w_hat_i / (d_i - lambda_j))_i / norm,   K_hat v_j = (sigma_i v_ji for the Sigma rows; -1),
+// the last entry because sum_i w_hat_i^2 / (d_i - lambda_j) = -1 exactly for the modified
+// problem. Both vector sets are componentwise accurate and hence orthogonal to working precision,
+// whatever the spread of the singular values; K_hat differs from K only by w_hat - w, which is
+// checked against tol_bw ||w|| (a failed check, like a deflated rho pole, returns false).
+// V: n x n, column j at V + j n, rows in original order (row[]); U: nr x n with column stride nr
+// (row i < r is sigma_i's, row r the new row's); sf = float sigma in original order.
+__device__ bool ge_append_vectors(int n, int r, int nr, const float* dhi, const float* dlo, const float* w,
+                                  const int* row, const int* nxt, const float* tau, const int* org, const float* sf,
+                                  float* what, float* V, float* U, float wn2, float tol_bw, int* s_flag) {
+  const int t = threadIdx.x;
+  const float thr = 1e-7f * sqrtf(wn2);  // the deflation threshold of secular_cta
+  if (t == 0) *s_flag = 0;
+  __syncthreads();
+  for (int i = t; i < n; i += blockDim.x) {
+    float wh = 0.f;
+    if (fabsf(w[i]) > thr) {
+      const ff di{dhi[i], dlo[i]};
+      float prod = 1.f;
+      for (int j = 0; j < n; ++j) {
+        if (!(fabsf(w[j]) > thr)) continue;
+        const int o = org[j];
+        const float num = ff_sub_to_f(ff{dhi[o], dlo[o]}, di) + tau[j];  // lambda_j - d_i
+        const int nj = nxt[j];
+        if (nj < 0) {
+          prod *= num;
+        } else {
+          const int pj = j < i ? j : nj;
+          prod *= __fdividef(num, ff_sub_to_f(ff{dhi[pj], dlo[pj]}, di));
+        }
+      }
+      wh = copysignf(sqrtf(fmaxf(prod, 0.f)), w[i]);
+      if (!(fabsf(wh - w[i]) <= tol_bw * sqrtf(wn2))) atomicOr(s_flag, 1);
+    } else if (row[i] >= r) {
+      atomicOr(s_flag, 1);  // rho pole deflated: its left vector is not e_r
+    }
+    what[i] = wh;
+  }
+  __syncthreads();
+  if (*s_flag) return false;
+  // Unnormalised v_j (deflated j: e_j), entry by entry.
+  for (int idx = t; idx < n * n; idx += blockDim.x) {
+    const int j = idx / n, i = idx - j * n;
+    float v;
+    if (!(fabsf(w[j]) > thr)) {
+      v = (i == j) ? 1.f : 0.f;
+    } else if (what[i] == 0.f) {
+      v = 0.f;
+    } else {
+      const int o = org[j];
+      const float dl = ff_sub_to_f(ff{dhi[o], dlo[o]}, ff{dhi[i], dlo[i]}) + tau[j];  // lambda_j - d_i
+      v = -what[i] / dl;
+    }
+    V[(size_t)j * n + row[i]] = v;
+  }
+  __syncthreads();
+  // Normalise v_j and form u_j (one warp per column).
+  const int warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
+    float* v = V + (size_t)j * n;
+    float* u = U + (size_t)j * nr;
+    const bool defl = !(fabsf(w[j]) > thr);
+    float sv = 0.f, su = 0.f;
+    for (int i = lane; i < n; i += 32) sv += v[i] * v[i];
+    for (int i = lane; i < r; i += 32) {
+      const float x = sf[i] * v[i];
+      su += x * x;
+    }
+    sv = warp_sum(sv);
+    su = warp_sum(su);
+    const float iu = defl ? 1.f : rsqrtf(su + 1.f);
+    for (int i = lane; i < nr; i += 32) {  // from the unnormalised v
+      float x;
+      if (defl) x = (i == row[j]) ? 1.f : 0.f;  // deflated sigma pole: u = e_i
+      else x = i < r ? sf[i] * v[i] * iu : -iu;
+      u[i] = x;
+    }
+    __syncwarp();
+    const float iv = rsqrtf(sv);
+    for (int i = lane; i < n; i += 32) v[i] *= iv;
   }
   __syncthreads();
   return true;
@@ -385,6 +499,10 @@ __device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, con
   }
 }
 
+// Largest rank bucket the fast core serves: its four n x n float matrices fit in shared memory up
+// to k_max = 115, so the 128 bucket keeps the Jacobi core (three matrices).
+constexpr int kFastCoreMaxKB = 64;
+
 template <typename T>
 __host__ __device__ inline size_t core_fast_smem_bytes(int kmax) {
   const int n = kmax + 1;
@@ -442,7 +560,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     bf[i] = in.kind == kEntry ? (float)in.b[i] : 0.f;
   }
   const float rhof = (float)in.rho;
-  bool ok;
+  bool ok, ge = false;
   if (in.kind != kEntry) {
     // Ascending poles: (0 for the rho column when grew), sigma_{r-1}^2, ..., sigma_0^2.
     const int off = in.grew ? 1 : 0;
@@ -463,23 +581,39 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     }
     __syncthreads();
     ISVD_STAMP(1);
-    ok = secular_cta<kTerms>(n, dhi, dlo, wv, rowmap, V, n, lhi, llo, nxt, s_sc, &s_flag);
+    float* tau = vec + 9 * n;
+    float* what = vec + 10 * n;
+    int* org = reinterpret_cast<int*>(vec + 11 * n);
+    ok = secular_cta<kTerms>(n, dhi, dlo, wv, rowmap, V, n, lhi, llo, nxt, s_sc, &s_flag, tau, org);
     ISVD_STAMP(2);
+    if (ok) {
+      ge = ge_append_vectors(n, r, nr, dhi, dlo, wv, rowmap, nxt, tau, org, sf, what, V, W, s_sc[0],
+                             kGeTolEps * Eps<float>::v, &s_flag);
+      // Correction rejected: vectors from w, then the Gram verification below.
+      if (!ge) ok = secular_cta<kTerms>(n, dhi, dlo, wv, rowmap, V, n, lhi, llo, nxt, s_sc, &s_flag);
+    }
   } else {
-    // 2 x 2 eigen-split of [[mu, 1], [1, 0]]: K^T K = Sigma^2 + m1 u1 u1^T + m0 u0 u0^T.
-    __shared__ double s_mu;
+    // 2 x 2 eigen-split of [[mu, 1], [1, 0]]: K^T K = Sigma^2 + m1 u1 u1^T + m0 u0 u0^T. The FP64
+    // scalars are computed once (thread 0) and shared.
+    __shared__ double s_m[6];
     if (t < 32) {
       double s_ = 0.0;
       for (int i = t; i < r; i += 32) s_ += in.a[i] * in.a[i];
       s_ = warp_sum(s_);
-      if (t == 0) s_mu = in.delta * in.delta * s_;
+      if (t == 0) {
+        const double mu = in.delta * in.delta * s_;
+        const double disc = sqrt(0.25 * mu * mu + 1.0);
+        const double m1 = 0.5 * mu + disc, m0 = 0.5 * mu - disc;
+        s_m[0] = m1;
+        s_m[1] = m0;
+        s_m[2] = sqrt(m1 * m1 + 1.0);
+        s_m[3] = sqrt(m0 * m0 + 1.0);
+        s_m[4] = sqrt(m1);
+        s_m[5] = sqrt(-m0);
+      }
     }
     __syncthreads();
-    const double mu = s_mu;
-    const double disc = sqrt(0.25 * mu * mu + 1.0);
-    const double m1 = 0.5 * mu + disc, m0 = 0.5 * mu - disc;
-    const double n1 = sqrt(m1 * m1 + 1.0), n0 = sqrt(m0 * m0 + 1.0);
-    const double sm1 = sqrt(m1);
+    const double m1 = s_m[0], m0 = s_m[1], n1 = s_m[2], n0 = s_m[3], sm1 = s_m[4];
     for (int s_ = t; s_ < n; s_ += blockDim.x) {
       const int i = r - 1 - s_;
       const double bi = in.b[i], ci = in.delta * in.sig[i] * in.a[i];
@@ -495,7 +629,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     if (ok) {
       // Second update in the eigenbasis of the first: diag(lam) + m0 z z^T (z = Q1^T u0), solved
       // as -(diag(-lam) + |m0| z z^T); ascending poles -lam_{n-1}, ..., -lam_0.
-      const float sm0 = (float)sqrt(-m0);
+      const float sm0 = (float)s_m[5];
       for (int s_ = t; s_ < n; s_ += blockDim.x) {
         const int j = n - 1 - s_;
         float acc = 0.f;
@@ -522,7 +656,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   int pass = 0;
   // S = W^T W and Q = V^T V (R = I - Q): S into B, Q into the scratch area after W.
   float* Qm = W + (size_t)(n + 1) * n;  // n x n (reuses the tail of the work area)
-  for (;; ++pass) {
+  for (; !ge; ++pass) {
     structured_kv(in, nr, n, V, W, tmp, sf, xf, bf, rhof);
     if (t < 2) s_max[t] = 0.f;
     smem_two_syrk(n, nr, W, V, B, Qm);
@@ -578,9 +712,9 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     for (int idx = t; idx < n * n; idx += blockDim.x) V[idx] += B[idx];
     __syncthreads();
   }
-  if (t == 0) *iters = pass;
+  if (t == 0) *iters = ge ? 2 : pass;
   ISVD_STAMP(4);
-  // W = K V is current. Column norms of W, and the singular values ||K v_j|| / ||v_j|| in
+  // W holds K V (Gram path) or the normalised left vectors (corrected-weight path). Column norms of W, and the singular values ||K v_j|| / ||v_j|| in
   // float-float arithmetic through K's structure (FP64-class accuracy on the FP32 pipes).
   const int lane = t & 31, warp = t >> 5;
   double* sref = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(nxt + n) + 15) & ~uintptr_t(15));
@@ -601,7 +735,14 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     }
   }
   __syncthreads();
-  const ff rho_ff = ff_of(in.rho);
+  __shared__ float s_rho[2];
+  if (t == 0) {
+    const ff q = ff_of(in.rho);
+    s_rho[0] = q.hi;
+    s_rho[1] = q.lo;
+  }
+  __syncthreads();
+  const ff rho_ff{s_rho[0], s_rho[1]};
   float* acc_hi = vec + 10 * n;  // per-column ||K v||^2 and ||v||^2 as float pairs
   float* acc_lo = vec + 11 * n;
   float* nv_hi = vec + 12 * n;
@@ -618,7 +759,8 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
       float s2 = 0.f;
       ff nv{0.f, 0.f}, acc{0.f, 0.f}, dot{0.f, 0.f};
       if (live) {
-        for (int row = g; row < nr; row += kSecLanes) s2 += W[(size_t)j * nr + row] * W[(size_t)j * nr + row];
+        if (!ge)
+          for (int row = g; row < nr; row += kSecLanes) s2 += W[(size_t)j * nr + row] * W[(size_t)j * nr + row];
         for (int i = g; i < n; i += kSecLanes) nv = ff_add(nv, two_prod(v[i], v[i]));
       }
       if (in.kind == kEntry) {
@@ -654,8 +796,8 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
         acc_lo[j] = acc.lo;
         nv_hi[j] = nv.hi;
         nv_lo[j] = nv.lo;
-        nrm[j] = (double)sqrtf(s2);
-        inv_nrm[j] = s2 > 0.f ? rsqrtf(s2) : 0.f;
+        nrm[j] = ge ? 1.0 : (double)sqrtf(s2);
+        inv_nrm[j] = ge ? 1.f : (s2 > 0.f ? rsqrtf(s2) : 0.f);
       }
     }
   }
@@ -691,7 +833,8 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   const int k_out = in.kt < nc ? in.kt : nc;
   // A kept singular value at the FP32 noise floor has no reliable left vector here (one warp,
   // FP32, on the reciprocal norms: small ||W_j|| <=> large 1 / ||W_j||).
-  if (warp == 0) {
+  if (warp == 0 && ge && lane == 0) s_flag = 0;
+  if (warp == 0 && !ge) {
     float mx = 0.f;
     for (int j = lane; j < n; j += 32) mx = fmaxf(mx, inv_nrm[j] > 0.f ? 1.f / inv_nrm[j] : 0.f);
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));

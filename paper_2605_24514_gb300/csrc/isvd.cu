@@ -13,28 +13,34 @@
 
 #include "../../include/isvd.h"
 #include "pool_kernels.cuh"
+#include "pool_warp.cuh"
 #include "refresh_kernels.cuh"
 #include "update_kernels.cuh"
 
 using namespace isvd;
 
 struct isvd_ctx {
+  // Fields a batched submit reads or advances for every op, packed into the first two cache
+  // lines (a pool touches thousands of these per tick).
+  int64_t m = 0, n = 0, t = 0, row_cap = 0, col_cap = 0;
+  int kmax = 0, ld = 0;
+  double tol_rel = 1e-10;
+  void* U = nullptr;
+  void* V = nullptr;
+  void* A = nullptr;
+  DevState* st = nullptr;
+  double* sig = nullptr;
+  int sticky = ISVD_OK;
   int prec = ISVD_FP64;
   size_t es = 8;
   int dev = 0;
   cudaStream_t stream = nullptr;
-  int64_t m = 0, n = 0, row_cap = 0, col_cap = 0;
-  int kmax = 0, ld = 0, k_host = 0;
-  double tol_rel = 1e-10, orth_tol = 1e-12;
+  int k_host = 0;
+  double orth_tol = 1e-12;
   int64_t orth_every = 0, since_orth = 0;
-  void* U = nullptr;
-  void* V = nullptr;
-  void* A = nullptr;
   void* Uref = nullptr;
   int64_t m_ref = 0, uref_cap = 0;
   int r_ref = 0;
-  DevState* st = nullptr;
-  double* sig = nullptr;
   double* p = nullptr;
   double* part = nullptr;
   void* UK = nullptr;
@@ -73,10 +79,9 @@ struct isvd_ctx {
   int64_t rsvd_calls = 0;
   isvd_policy pol{};
   int has_pol = 0;
-  int64_t t = 0, t_last = 0, refreshes = 0, reorths = 0, launches = 0;
+  int64_t t_last = 0, refreshes = 0, reorths = 0, launches = 0;
   double orth_err_u = 0, orth_err_v = 0;
   isvd_metrics_t last_check{};
-  int sticky = ISVD_OK;
   std::string err;
   // profiling (events around launches; per-update stamps)
   int prof = 0;
@@ -191,7 +196,7 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 template <typename T>
 size_t core_kernel_smem(int kmax) {
   size_t b = core_smem_bytes<T>(kmax);
-  if (sizeof(T) == sizeof(float)) b = std::max(b, core_fast_smem_bytes<T>(kmax));
+  if (sizeof(T) == sizeof(float) && kb_bucket(kmax) <= kFastCoreMaxKB) b = std::max(b, core_fast_smem_bytes<T>(kmax));
   return 2 * (kKmaxLimit + 1) * sizeof(double) + b;
 }
 
@@ -244,11 +249,17 @@ isvd_status set_attrs(isvd_ctx* h) {
   if ((s = set_rot_attr<T, 16>(h)) || (s = set_rot_attr<T, 32>(h)) || (s = set_rot_attr<T, 64>(h)) ||
       (s = set_rot_attr<T, 128>(h)))
     return s;
-  const size_t cs = core_kernel_smem<T>(h->kmax);
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+  // The attribute is process-wide per template, so each bucket gets the shared memory of the
+  // largest k_max it serves (handles with different k_max share one instantiation).
+  const int kcap = sizeof(T) == sizeof(double) ? 96 : kKmaxLimit;
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_kernel_smem<T>(16)));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_kernel_smem<T>(32)));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_kernel_smem<T>(64)));
+  CK(h, cudaFuncSetAttribute(k_core<T, T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_kernel_smem<T>(kcap)));
   CK(h, cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_chol_rinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -463,7 +474,7 @@ isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
 // C (rc x cc, FP64) = X^T Y over `rows` rows.
 template <typename T>
 isvd_status gemm_tn(isvd_ctx* h, const T* X, int64_t ldx, int cx, const T* Y, int64_t ldy, int cy, int64_t rows,
-                    double* C) {
+                    double* C, bool exact = false) {
   CK(h, cudaMemsetAsync(C, 0, (size_t)cx * cy * 8, h->stream));
   if (rows <= 0) return ISVD_OK;
   const int64_t splits_target = 304;
@@ -471,24 +482,38 @@ isvd_status gemm_tn(isvd_ctx* h, const T* X, int64_t ldx, int cx, const T* Y, in
   rps = std::max<int64_t>(kTnChunk, (rps + kTnChunk - 1) / kTnChunk * kTnChunk);
   dim3 grid((unsigned)((cx + kTnTile - 1) / kTnTile), (unsigned)((cy + kTnTile - 1) / kTnTile),
             (unsigned)((rows + rps - 1) / rps));
-  k_gemm_tn<T><<<grid, 256, 0, h->stream>>>(X, ldx, cx, Y, ldy, cy, rows, rps, C, cy);
+  if (exact) k_gemm_tn<T, true><<<grid, 256, 0, h->stream>>>(X, ldx, cx, Y, ldy, cy, rows, rps, C, cy);
+  else k_gemm_tn<T><<<grid, 256, 0, h->stream>>>(X, ldx, cx, Y, ldy, cy, rows, rps, C, cy);
   CKL(h);
   return ISVD_OK;
 }
 
+// Eigendecomposition of the FP64 Gram matrix: FP64 Jacobi for FP64 storage (rotations in shared
+// memory up to n = 80, beyond that in the n x n FP64 scratch vk), FP32 Jacobi with FP64
+// Rayleigh-quotient eigenvalues for FP32 storage.
 template <typename T>
-isvd_status sym_eig(isvd_ctx* h, const double* G, int n, double* evals, double* evecs, int fp64) {
+isvd_status sym_eig(isvd_ctx* h, const double* G, int n, double* evals, double* evecs, int fp64, double* vk) {
   const int threads = core_threads(std::max(n - 1, 1));
   if (fp64 && n <= 80) {
     const size_t sm = (size_t)2 * n * n * sizeof(double) + (size_t)n * 12 + 64;
-    k_sym_eig<double><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info);
+    k_sym_eig<double><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info, nullptr);
+  } else if (fp64) {
+    const size_t sm = (size_t)n * n * sizeof(double) + (size_t)n * 12 + 64;
+    k_sym_eig<double><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info, vk);
   } else {
     const size_t sm = (size_t)2 * n * n * sizeof(float) + (size_t)n * 12 + 64;
-    k_sym_eig<float><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info);
+    k_sym_eig<float><<<1, threads, sm, h->stream>>>(G, n, evals, evecs, h->info, nullptr);
   }
   CKL(h);
   return ISVD_OK;
 }
+
+// Columns of a freshly formed factor side Q = A W diag(1 / sigma) (rows x r, row stride ldq)
+// whose singular value is at the rounding floor are seeded with pseudo-random values, then the
+// side is re-orthonormalised by shifted CholeskyQR3 (the leading columns barely move; the
+// seeded ones become an orthonormal completion).
+template <typename T>
+isvd_status finish_side(isvd_ctx* h, T* Q, int64_t rows, int r, const double* sig);
 
 
 isvd_status read_state(isvd_ctx* h, DevState* out) {
@@ -504,11 +529,13 @@ isvd_status read_state(isvd_ctx* h, DevState* out) {
 // first pass with a small diagonal shift (robust when Q is rank deficient), then two plain
 // passes (Fukaya et al.'s shifted CholeskyQR3).
 template <typename T>
-isvd_status orth_cols(isvd_ctx* h, T* Q, int64_t rows, int l) {
+isvd_status orth_cols(isvd_ctx* h, T* Q, int64_t rows, int l, int64_t ldq = -1) {
   isvd_status s;
+  if (ldq < 0) ldq = l;
   double* B = h->small + 4 * kSmall;
+  if ((s = ensure_buf(h, &h->Rl, &h->rl_cap, (int64_t)l * l * (int64_t)h->es * 2))) return s;
   for (int pass = 0; pass < 3; ++pass) {
-    if ((s = gemm_tn<T>(h, Q, l, l, Q, l, l, rows, B))) return s;
+    if ((s = gemm_tn<T>(h, Q, ldq, l, Q, ldq, l, rows, B))) return s;
     if (pass == 0) {
       k_add_diag<<<1, 128, 0, h->stream>>>(B, l, sizeof(T) == 8 ? 1e-13 : 1e-5);
       CKL(h);
@@ -519,7 +546,7 @@ isvd_status orth_cols(isvd_ctx* h, T* Q, int64_t rows, int l) {
     RotSide sq{};
     sq.X = sq.Y = Q;
     sq.rows = rows;
-    sq.ldx = sq.ldy = l;
+    sq.ldx = sq.ldy = ldq;
     sq.R = h->Rl;
     sq.ldr = l;
     sq.c_in = l;
@@ -528,6 +555,43 @@ isvd_status orth_cols(isvd_ctx* h, T* Q, int64_t rows, int l) {
     if ((s = launch_rotate<T>(h, sq, none, kb_bucket(l), (const T*)nullptr, nullptr))) return s;
   }
   return ISVD_OK;
+}
+
+// One-sided finish of a truncated SVD (Gram or randomized path). Given B = A W (or A^T W) for the
+// computed orthonormal basis W of the other side (rows x r, storage TB, row stride ldb), the
+// singular values are taken as the column norms ||B_j|| (FP64 sums): accurate down to the
+// rounding level of A, where sqrt of the Gram eigenvalue only reaches sqrt(eps) sigma_1. Columns
+// are sorted by them; outB = B diag(1 / sigma) and W are permuted alike, and outB is finished by
+// finish_side (seed + re-orthonormalisation).
+template <typename T, typename TB>
+isvd_status one_sided_finish(isvd_ctx* h, const TB* B, int64_t ldb, T* outB, int64_t rows, T* W, int64_t rows_w,
+                             int r, double* sig_o) {
+  double* sq = h->small + 5 * kSmall;
+  int* perm = reinterpret_cast<int*>(sq + 256);
+  CK(h, cudaMemsetAsync(sq, 0, (size_t)r * 8, h->stream));
+  const int64_t splits = std::min<int64_t>(256, std::max<int64_t>(1, rows / 512));
+  const int64_t rps = (rows + splits - 1) / splits;
+  const dim3 gs((unsigned)((r + 31) / 32), (unsigned)splits);
+  k_col_sumsq<TB><<<gs, 256, 0, h->stream>>>(B, rows, ldb, r, rps, sq);
+  CKL(h);
+  k_sort_norms<<<1, 128, 0, h->stream>>>(sq, r, sig_o, perm, h->inv);
+  CKL(h);
+  k_permute_cols<TB, T><<<(unsigned)((rows + 7) / 8), 256, 0, h->stream>>>(B, ldb, outB, h->ld, rows, r, perm, h->inv);
+  CKL(h);
+  k_permute_cols<T, T><<<(unsigned)((rows_w + 7) / 8), 256, 0, h->stream>>>(W, h->ld, W, h->ld, rows_w, r, perm, nullptr);
+  CKL(h);
+  return finish_side<T>(h, outB, rows, r, sig_o);
+}
+
+template <typename T>
+isvd_status finish_side(isvd_ctx* h, T* Q, int64_t rows, int r, const double* sig) {
+  if (r < 1 || rows < r) return ISVD_OK;
+  const double rel = sizeof(T) == sizeof(double) ? 1e-13 : 1e-5;  // ~64 eps: B_j is rounding there
+  const int64_t tot = rows * r;
+  k_seed_small_cols<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(Q, rows, h->ld, sig, r, rel,
+                                                                             h->seed ^ 0x5EEDC0151ull);
+  CKL(h);
+  return orth_cols<T>(h, Q, rows, r, h->ld);
 }
 
 // Randomized truncated SVD of A (Halko, Martinsson and Tropp 2011) at rank kr: l = kr + p
@@ -576,7 +640,7 @@ isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, in
   double* GB = h->small + 3 * kSmall;
   double* evecs = h->small + 2 * kSmall;
   if ((s = gemm_tn<double>(h, h->Zd, l, l, h->Zd, l, l, n, GB))) return s;
-  if ((s = sym_eig<T>(h, GB, l, h->evals, evecs, sizeof(T) == 8))) return s;
+  if ((s = sym_eig<T>(h, GB, l, h->evals, evecs, sizeof(T) == 8, h->small + kSmall))) return s;
   k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, l, kr, sig_o, h->inv, Rl2, l, h->scal + 3);
   CKL(h);
   RotSide su{};
@@ -591,9 +655,12 @@ isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, in
   su.k_out = kr;
   RotSide none{};
   if ((s = launch_rotate<T>(h, su, none, kb_bucket(l), (const T*)nullptr, nullptr))) return s;
-  k_small_gemm_cast<T><<<(unsigned)((n * kr + 255) / 256), 256, 0, h->stream>>>(h->Zd, n, l, evecs, kr, h->inv, Vo,
-                                                                                h->ld);
+  // B = A^T U = Z E[:, :kr] (FP64), then the one-sided finish of V.
+  if ((s = ensure_buf(h, (void**)&h->Cbuf, &h->cbuf_cap, n * kr * 8))) return s;
+  k_small_gemm_cast<double><<<(unsigned)((n * kr + 255) / 256), 256, 0, h->stream>>>(h->Zd, n, l, evecs, kr, nullptr,
+                                                                                     h->Cbuf, kr);
   CKL(h);
+  if ((s = one_sided_finish<T, double>(h, h->Cbuf, kr, Vo, n, Uo, m, kr, sig_o))) return s;
   k_tail_from_N<<<1, 32, 0, h->stream>>>(h->st, sig_o, kr, h->scal + 1);
   CKL(h);
   return ISVD_OK;
@@ -611,12 +678,13 @@ isvd_status tsvd(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm = 1)
   if (std::min(m, n) > kKmaxLimit) return tsvd_randomized<T>(h, kr, Uo, sig_o, Vo, warm);
   isvd_status s;
   const int q = (int)std::min(m, n);
-  if ((s = ensure_buf(h, (void**)&h->G, &h->G_cap, (int64_t)q * q * 8 * 2))) return s;
+  if ((s = ensure_buf(h, (void**)&h->G, &h->G_cap, (int64_t)q * q * 8 * 3))) return s;
   double* G = h->G;
   double* evecs = h->G + (int64_t)q * q;
+  double* vk = h->G + (int64_t)2 * q * q;
   if (n <= m) {
-    if ((s = gemm_tn<T>(h, A, lda, (int)n, A, lda, (int)n, m, G))) return s;
-    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64))) return s;
+    if ((s = gemm_tn<T>(h, A, lda, (int)n, A, lda, (int)n, m, G, true))) return s;
+    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64, vk))) return s;
     k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, q, kr, sig_o, h->inv, Vo, h->ld, h->scal + 1);
     CKL(h);
     RotSide su{};
@@ -629,18 +697,19 @@ isvd_status tsvd(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm = 1)
     su.ldr = h->ld;
     su.c_in = (int)n;
     su.k_out = kr;
-    su.colscale = h->inv;
+    su.colscale = nullptr;  // B = A V; sigma and the scaling come from its column norms
     RotSide none{};
     none.rows = 0;
     none.c_in = 0;
     none.k_out = 0;
     if ((s = launch_rotate<T>(h, su, none, kb_bucket(std::max<int>((int)n, kr)), (const T*)nullptr, nullptr))) return s;
+    if ((s = one_sided_finish<T, T>(h, Uo, h->ld, Uo, m, Vo, n, kr, sig_o))) return s;
   } else {
     CK(h, cudaMemsetAsync(G, 0, (size_t)q * q * 8, h->stream));
     const int64_t e = (int64_t)m * m;
     k_gram_rows<T><<<(unsigned)((e + 7) / 8), 256, 0, h->stream>>>(A, lda, (int)m, n, G);
     CKL(h);
-    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64))) return s;
+    if ((s = sym_eig<T>(h, G, q, h->evals, evecs, fp64, vk))) return s;
     k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, q, kr, sig_o, h->inv, Uo, h->ld, h->scal + 1);
     CKL(h);
     // V = A^T U S^-1.
@@ -650,9 +719,7 @@ isvd_status tsvd(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm = 1)
     dim3 grid((unsigned)((n + kTnTile - 1) / kTnTile), (unsigned)((kr + kTnTile - 1) / kTnTile), 1);
     k_gemm_tn<T><<<grid, 256, 0, h->stream>>>(A, lda, (int)n, Uo, h->ld, kr, m, rps, h->Cbuf, kr);
     CKL(h);
-    const int64_t tot = n * kr;
-    k_scale_cast<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->Cbuf, n, kr, kr, h->inv, Vo, h->ld);
-    CKL(h);
+    if ((s = one_sided_finish<T, double>(h, h->Cbuf, kr, Vo, n, Uo, m, kr, sig_o))) return s;
   }
   return ISVD_OK;
 }
@@ -716,7 +783,7 @@ isvd_status max_angle(isvd_ctx* h, const T* Q1, int64_t rows1, int r1, const T* 
   }
   k_angle_matrix<<<1, 256, 0, h->stream>>>(B, C, r1, r2, tr, E);
   CKL(h);
-  if ((s = sym_eig<T>(h, E, q, h->evals, evecs, sizeof(T) == sizeof(double)))) return s;
+  if ((s = sym_eig<T>(h, E, q, h->evals, evecs, sizeof(T) == sizeof(double), h->small + 4 * kSmall))) return s;
   double lam = 0;
   CK(h, cudaMemcpyAsync(&lam, h->evals, 8, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -1211,6 +1278,16 @@ int64_t isvd_kernel_launches(isvd_t h) { return h ? h->launches : 0; }
 int isvd_debug_core_clock(long long* out) {
   return (int)cudaMemcpyFromSymbol(out, isvd_core_clock, sizeof(long long) * 16);
 }
+int isvd_debug_clock_sums(unsigned long long* out, int reset) {
+  int e = (int)cudaMemcpyFromSymbol(out, isvd_core_clock_sum, sizeof(unsigned long long) * 32);
+  if (!e) e = (int)cudaMemcpyFromSymbol(out + 32, isvd_core_clock_cnt, sizeof(unsigned long long) * 32);
+  if (!e && reset) {
+    unsigned long long z[32] = {};
+    e = (int)cudaMemcpyToSymbol(isvd_core_clock_sum, z, sizeof(z));
+    if (!e) e = (int)cudaMemcpyToSymbol(isvd_core_clock_cnt, z, sizeof(z));
+  }
+  return e;
+}
 #endif
 
 isvd_status isvd_profile(isvd_t h, int enable) {
@@ -1269,7 +1346,30 @@ struct isvd_pool_ctx {
   void* payload = nullptr;
   int64_t payload_cap = 0;
   cudaEvent_t copied = nullptr;
-  int64_t launches = 0, ticks = 0, fused_ops = 0, fallback_ops = 0;
+  int* retry_list = nullptr;  // per-tick list of warp-path updates handed to the CTA kernel
+  int64_t retry_cap = 0;
+  int* retry_n = nullptr;     // one counter per tick of a submit
+  int64_t retry_n_cap = 0;
+  void* rot_scratch = nullptr;  // per-update records from the warp kernel to the rotation kernel
+  int64_t rot_cap = 0;          // updates
+  int* chunks_pinned = nullptr;  // first rotation block of each update (per bucket run)
+  int* chunks_dev = nullptr;
+  int64_t chunks_cap = 0;
+  int* block_op = nullptr;  // rotation block -> update, written by the warp kernels
+  int64_t block_op_cap = 0;
+  // The rank buckets of a tick run concurrently on side streams (fork/join through events).
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_w[3] = {nullptr, nullptr, nullptr}, ev_r[3] = {nullptr, nullptr, nullptr};
+  int num_sms = 152;
+  // Per-stream scratch of a submit (valid where s_gen == gen), so that a submit touches only the
+  // streams it names, and each stream's fused-kernel bucket (set at admission).
+  std::vector<int64_t> s_m, s_n;
+  std::vector<uint32_t> s_gen;
+  std::vector<int32_t> s_seen;
+  std::vector<uint8_t> s_bucket;
+  uint32_t gen = 0;
+  std::vector<int32_t> touched;
+  int64_t launches = 0, ticks = 0, fused_ops = 0, fallback_ops = 0, warp_ops = 0;
   std::string err;
 };
 
@@ -1285,6 +1385,43 @@ isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
   k_pool_tick<KB><<<count, pool_threads(KB), pool_smem_bytes<KB>(), p->stream>>>(ops);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool tick launch: ") + cudaGetErrorString(e));
+  p->launches++;
+  return ISVD_OK;
+}
+
+// One warp-per-update launch over ops[0 .. count) of rank bucket KB in tick t; hand-backs are
+// listed as base + index into the tick's warp ops.
+template <int KB>
+isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, int base, int t,
+                             const int* chunks, int* block_op) {
+  const int blocks = (count + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  auto* scr = reinterpret_cast<RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
+  k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), cs>>>(ops, count, base, p->retry_list,
+                                                                             p->retry_n + t, scr, chunks, block_op);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
+  p->launches++;
+  return ISVD_OK;
+}
+
+// Row-parallel rotations of a bucket run (chunks = its first-block table, nblocks in total).
+template <int KB>
+isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int base, const int* chunks,
+                               const int* block_op, int nblocks) {
+  auto* scr = reinterpret_cast<const RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
+  k_pool_rotate<KB><<<nblocks, kPoolRotRows, 0, cs>>>(ops, scr, chunks, block_op);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
+  p->launches++;
+  return ISVD_OK;
+}
+
+// The CTA kernel over the updates the warps of tick t handed back (ops = the tick's warp ops).
+isvd_status pool_launch_retry(isvd_pool_ctx* p, const PoolOp* ops, int count, int t) {
+  const int rblocks = std::min(count, p->num_sms);
+  k_pool_retry<32><<<rblocks, pool_threads(32), pool_smem_bytes<32>(), p->stream>>>(ops, p->retry_list, p->retry_n + t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool retry launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
 }
@@ -1317,11 +1454,31 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->cfg.cuda_stream = cfg->cuda_stream;
   p->cfg.orth_every = (int64_t)1 << 62;  // the pool path runs no monitor; isvd_reorthogonalize on demand
   p->cfg.rsvd_power_iters = -1;
-  cudaError_t e = cudaSuccess;
-  switch (p->kb) {
-    case 16: e = cudaFuncSetAttribute(k_pool_tick<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<16>()); break;
-    case 32: e = cudaFuncSetAttribute(k_pool_tick<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>()); break;
-    default: e = cudaFuncSetAttribute(k_pool_tick<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<64>()); break;
+  cudaError_t e = cudaFuncSetAttribute(k_pool_tick<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_tick<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_tick<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_tick<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_retry<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_warp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_warp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<32>());
+  if (e == cudaSuccess) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_w[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_r[i], cudaEventDisableTiming);
   }
   if (e != cudaSuccess || cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming) != cudaSuccess) {
     delete p;
@@ -1337,6 +1494,18 @@ void isvd_pool_destroy(isvd_pool_t p) {
   for (isvd_ctx* h : p->streams)
     if (h) isvd_destroy(h);
   if (p->ops_dev) cudaFree(p->ops_dev);
+  if (p->retry_list) cudaFree(p->retry_list);
+  if (p->retry_n) cudaFree(p->retry_n);
+  if (p->rot_scratch) cudaFree(p->rot_scratch);
+  if (p->block_op) cudaFree(p->block_op);
+  for (int i = 0; i < 3; ++i) {
+    if (p->side[i]) cudaStreamDestroy(p->side[i]);
+    if (p->ev_w[i]) cudaEventDestroy(p->ev_w[i]);
+    if (p->ev_r[i]) cudaEventDestroy(p->ev_r[i]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->chunks_dev) cudaFree(p->chunks_dev);
+  if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
   if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
   if (p->payload) cudaFree(p->payload);
   if (p->copied) cudaEventDestroy(p->copied);
@@ -1351,9 +1520,10 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   for (isvd_ctx* h : p->streams) live += h != nullptr;
   if (live >= p->max_streams) return pool_fail(p, ISVD_EBUDGET, "pool: stream slots exhausted");
   isvd_config c = p->cfg;
+  c.k_max = k;  // the stream's rank capacity selects its fused-kernel bucket
   c.row_cap = std::max<int64_t>(row_cap, m0 + 1);
   c.col_cap = std::max<int64_t>(col_cap, n0 + 1);
-  const int64_t need = stream_footprint(c.row_cap, c.col_cap, round_up(p->kmax, 4));
+  const int64_t need = stream_footprint(c.row_cap, c.col_cap, round_up(k, 4));
   if (p->budget > 0 && p->used + need > p->budget)
     return pool_fail(p, ISVD_EBUDGET, "pool: HBM budget exceeded (" + std::to_string(p->used + need) + " > " +
                                           std::to_string(p->budget) + " bytes)");
@@ -1375,6 +1545,16 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   }
   p->streams[id] = h;
   p->bytes[id] = need;
+  if (p->s_gen.size() < p->streams.size()) {
+    const size_t ns = p->streams.size();
+    p->s_m.resize(ns);
+    p->s_n.resize(ns);
+    p->s_gen.resize(ns, 0);
+    p->s_seen.resize(ns);
+    p->s_bucket.resize(ns);
+  }
+  p->s_gen[id] = 0;
+  p->s_bucket[id] = (uint8_t)pool_bucket(k);
   p->used += need;
   *stream_id = id;
   return ISVD_OK;
@@ -1404,22 +1584,33 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   if (!p || (nops > 0 && !ops)) return ISVD_EINVAL;
   if (nops == 0) return ISVD_OK;
   const size_t es = 4;
-  // Validate every op against the shapes it will see (per-stream order), before any work.
-  std::vector<int64_t> mm(p->streams.size()), nn(p->streams.size());
-  std::vector<int32_t> seen(p->streams.size(), 0);
+  // Validate every op against the shapes it will see (per-stream order), before any work. Only
+  // the streams named by the ops are read (their shapes into the pool's per-stream scratch).
+  if (++p->gen == 0) {
+    std::fill(p->s_gen.begin(), p->s_gen.end(), 0u);
+    p->gen = 1;
+  }
+  const uint32_t gen = p->gen;
+  std::vector<int64_t>& mm = p->s_m;
+  std::vector<int64_t>& nn = p->s_n;
+  std::vector<int32_t>& seen = p->s_seen;
+  p->touched.clear();
   std::vector<int32_t> tick_of(nops);
   int32_t nticks = 0;
-  for (size_t s_ = 0; s_ < p->streams.size(); ++s_)
-    if (p->streams[s_]) {
-      mm[s_] = p->streams[s_]->m;
-      nn[s_] = p->streams[s_]->n;
-      if (p->streams[s_]->sticky) return (isvd_status)p->streams[s_]->sticky;
-    }
   for (int64_t e = 0; e < nops; ++e) {
     const isvd_op& o = ops[e];
     if (o.stream < 0 || o.stream >= (int32_t)p->streams.size() || !p->streams[o.stream])
       return pool_fail(p, ISVD_EINVAL, "pool op " + std::to_string(e) + ": unknown stream");
     const int32_t sid = o.stream;
+    if (p->s_gen[sid] != gen) {
+      const isvd_ctx* h = p->streams[sid];
+      if (h->sticky) return (isvd_status)h->sticky;
+      p->s_gen[sid] = gen;
+      mm[sid] = h->m;
+      nn[sid] = h->n;
+      seen[sid] = 0;
+      p->touched.push_back(sid);
+    }
     if (o.kind == kEntry) {
       if (o.i < 0 || o.i >= mm[sid] || o.j < 0 || o.j >= nn[sid] || !std::isfinite(o.delta))
         return pool_fail(p, ISVD_EBOUNDS, "pool op " + std::to_string(e) + ": entry out of range");
@@ -1461,6 +1652,24 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   {
     std::vector<int64_t> fill(tick_start.begin(), tick_start.end() - 1);
     for (int64_t e = 0; e < nops; ++e) order[fill[tick_of[e]]++] = e;
+    // Within a tick: first the appends of rank capacity <= 32 (one warp-per-update launch, the
+    // widest buckets first so the longest updates start first), then the CTA kernel's updates
+    // grouped by rank bucket (one launch per bucket, the narrowest instance that fits).
+    // Counting sort (stable) on a small key: 0-2 warp buckets 32/16/8, 3-6 CTA buckets 8-64.
+    std::vector<uint8_t> key(nops);
+    for (int64_t e = 0; e < nops; ++e) {
+      const int b = p->s_bucket[ops[e].stream];
+      const int lb = b == 8 ? 0 : b == 16 ? 1 : b == 32 ? 2 : 3;
+      key[e] = (uint8_t)((ops[e].kind != kEntry && b <= kWarpKB) ? 2 - lb : 3 + lb);
+    }
+    std::vector<int64_t> tmp(nops);
+    for (int32_t t = 0; t < nticks; ++t) {
+      int64_t cnt[8] = {};
+      for (int64_t z = tick_start[t]; z < tick_start[t + 1]; ++z) cnt[key[order[z]] + 1]++;
+      for (int k = 1; k < 8; ++k) cnt[k] += cnt[k - 1];
+      for (int64_t z = tick_start[t]; z < tick_start[t + 1]; ++z) tmp[tick_start[t] + cnt[key[order[z]]]++] = order[z];
+      std::copy(tmp.begin() + tick_start[t], tmp.begin() + tick_start[t + 1], order.begin() + tick_start[t]);
+    }
   }
   if (nops > p->pinned_cap) {
     cudaEventSynchronize(p->copied);
@@ -1480,15 +1689,60 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       return pool_fail(p, ISVD_ENOMEM, "pool descriptors");
     }
   }
+  int64_t tick_max = 0;
+  for (int32_t t = 0; t < nticks; ++t) tick_max = std::max(tick_max, tick_start[t + 1] - tick_start[t]);
+  if (tick_max > p->retry_cap || nticks > p->retry_n_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (tick_max > p->retry_cap) {
+      if (p->retry_list) cudaFree(p->retry_list);
+      p->retry_list = nullptr;
+      p->retry_cap = std::max<int64_t>(tick_max, 2 * p->retry_cap);
+      if (cudaMalloc((void**)&p->retry_list, sizeof(int) * (size_t)p->retry_cap) != cudaSuccess) {
+        p->retry_cap = 0;
+        return pool_fail(p, ISVD_ENOMEM, "pool retry list");
+      }
+    }
+    if (nticks > p->retry_n_cap) {
+      if (p->retry_n) cudaFree(p->retry_n);
+      p->retry_n = nullptr;
+      p->retry_n_cap = std::max<int64_t>(nticks, 2 * p->retry_n_cap);
+      if (cudaMalloc((void**)&p->retry_n, sizeof(int) * (size_t)p->retry_n_cap) != cudaSuccess) {
+        p->retry_n_cap = 0;
+        return pool_fail(p, ISVD_ENOMEM, "pool retry counters");
+      }
+    }
+  }
+  if (tick_max > p->rot_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->rot_scratch) cudaFree(p->rot_scratch);
+    p->rot_scratch = nullptr;
+    p->rot_cap = std::max<int64_t>(tick_max, 2 * p->rot_cap);
+    if (cudaMalloc(&p->rot_scratch, kRotScratchStride * (size_t)p->rot_cap) != cudaSuccess) {
+      p->rot_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool rotation scratch");
+    }
+  }
+  if (nops > p->chunks_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->chunks_dev) cudaFree(p->chunks_dev);
+    if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
+    p->chunks_dev = nullptr;
+    p->chunks_pinned = nullptr;
+    p->chunks_cap = std::max<int64_t>(nops, 2 * p->chunks_cap);
+    if (cudaMalloc((void**)&p->chunks_dev, sizeof(int) * (size_t)p->chunks_cap) != cudaSuccess ||
+        cudaMallocHost((void**)&p->chunks_pinned, sizeof(int) * (size_t)p->chunks_cap) != cudaSuccess) {
+      p->chunks_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool rotation tables");
+    }
+  }
   cudaEventSynchronize(p->copied);  // the previous submit's descriptor copy has finished
   isvd_status s;
-  // Grow every stream to its final shape for this submit BEFORE building descriptors, so that no
-  // reallocation can invalidate a descriptor or copy data ahead of queued work.
-  for (size_t s_ = 0; s_ < p->streams.size(); ++s_) {
-    isvd_ctx* h = p->streams[s_];
-    if (!h) continue;
-    if ((s = ensure_rows(h, mm[s_] + 1))) return s;
-    if ((s = ensure_cols(h, nn[s_] + 1))) return s;
+  // Grow every named stream to its final shape for this submit BEFORE building descriptors, so
+  // that no reallocation can invalidate a descriptor or copy data ahead of queued work.
+  for (const int32_t sid : p->touched) {
+    isvd_ctx* h = p->streams[sid];
+    if ((s = ensure_rows(h, mm[sid] + 1))) return s;
+    if ((s = ensure_cols(h, nn[sid] + 1))) return s;
   }
   std::vector<char> fused(nops, 0);
   for (int32_t t = 0; t < nticks; ++t) {
@@ -1497,7 +1751,8 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       const isvd_op& o = ops[e];
       isvd_ctx* h = p->streams[o.stream];
       const int64_t prow = o.kind == kRow ? h->n : h->m;
-      fused[q] = (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
+      if (o.kind != kEntry && p->s_bucket[o.stream] <= kWarpKB) fused[q] = 2;  // warp per update
+      else fused[q] = (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
       PoolOp& d = p->ops_pinned[q];
       d.U = (float*)h->U;
       d.V = (float*)h->V;
@@ -1519,20 +1774,105 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       h->t += 1;
     }
   }
+  auto bucket_at = [&](int64_t z) { return (int)p->s_bucket[ops[order[z]].stream]; };
+  // Rotation block tables of the warp-kernel runs (one run per tick and rank bucket):
+  // chunks[q] = first block of update q within its run; run_blocks[first q of a run] = total.
+  std::vector<int> run_blocks(nops, 0);
+  for (int32_t t = 0; t < nticks; ++t) {
+    int64_t q = tick_start[t];
+    while (q < tick_start[t + 1]) {
+      if (fused[q] != 2) {
+        ++q;
+        continue;
+      }
+      int64_t b1 = q;
+      int tot = 0;
+      while (b1 < tick_start[t + 1] && fused[b1] == 2 && bucket_at(b1) == bucket_at(q)) {
+        const PoolOp& d = p->ops_pinned[b1];
+        const int64_t nP = d.kind == kRow ? d.n : d.m, nQ = d.kind == kRow ? d.m : d.n;
+        p->chunks_pinned[b1] = tot;
+        tot += (int)((nP + kPoolRotRows - 1) / kPoolRotRows + (nQ + kPoolRotRows - 1) / kPoolRotRows);
+        ++b1;
+      }
+      run_blocks[q] = tot;
+      q = b1;
+    }
+  }
+  // Each run's block -> update table sits at its own offset (runs of one tick run concurrently).
+  std::vector<int64_t> run_boff(nops, 0);
+  int64_t total_blocks = 0;
+  for (int64_t q = 0; q < nops; ++q)
+    if (run_blocks[q]) {
+      run_boff[q] = total_blocks;
+      total_blocks += run_blocks[q];
+    }
+  if (total_blocks > p->block_op_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->block_op) cudaFree(p->block_op);
+    p->block_op = nullptr;
+    p->block_op_cap = std::max<int64_t>(total_blocks, 2 * p->block_op_cap);
+    if (cudaMalloc((void**)&p->block_op, sizeof(int) * (size_t)p->block_op_cap) != cudaSuccess) {
+      p->block_op_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool rotation block table");
+    }
+  }
   if (cudaMemcpyAsync(p->ops_dev, p->ops_pinned, sizeof(PoolOp) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaMemcpyAsync(p->chunks_dev, p->chunks_pinned, sizeof(int) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
+          cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool descriptor copy");
   cudaEventRecord(p->copied, p->stream);
+  if (cudaMemsetAsync(p->retry_n, 0, sizeof(int) * (size_t)nticks, p->stream) != cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool retry counters");
   for (int32_t t = 0; t < nticks; ++t) {
     // Fused ops of the tick are contiguous runs; ops outside the fused kernel's limits take the
     // single-stream kernels, in the same stream order.
     int64_t q = tick_start[t];
+    auto bucket_of = [&](int64_t z) { return (int)p->s_bucket[ops[order[z]].stream]; };
     while (q < tick_start[t + 1]) {
       int64_t q2 = q;
-      while (q2 < tick_start[t + 1] && fused[q2] == fused[q]) ++q2;
-      if (fused[q]) {
+      while (q2 < tick_start[t + 1] && fused[q2] == fused[q] && (fused[q] != 1 || bucket_of(q2) == bucket_of(q))) ++q2;
+      if (fused[q] == 2) {
+        // Per rank bucket (contiguous runs, widest first) on its own side stream: the warp
+        // launch, then its rotation launch. The hand-back launch runs on the main stream once all
+        // warp launches are done; the tick joins when all rotations are done.
+        if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
+        int nrun = 0;
+        for (int64_t b0 = q; b0 < q2; ++nrun) {
+          int64_t b1 = b0;
+          while (b1 < q2 && bucket_of(b1) == bucket_of(b0)) ++b1;
+          const int cnt = (int)(b1 - b0), base = (int)(b0 - q);
+          cudaStream_t cs = p->side[nrun];
+          int* bop = p->block_op + run_boff[b0];
+          const int* ch = p->chunks_dev + b0;
+          if (cudaStreamWaitEvent(cs, p->ev_fork, 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
+          switch (bucket_of(b0)) {
+            case 8: s = pool_launch_warp<8>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
+            case 16: s = pool_launch_warp<16>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
+            default: s = pool_launch_warp<32>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
+          }
+          if (s) return s;
+          if (cudaEventRecord(p->ev_w[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
+          switch (bucket_of(b0)) {
+            case 8: s = pool_launch_rotate<8>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
+            case 16: s = pool_launch_rotate<16>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
+            default: s = pool_launch_rotate<32>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
+          }
+          if (s) return s;
+          if (cudaEventRecord(p->ev_r[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
+          b0 = b1;
+        }
+        for (int i = 0; i < nrun; ++i)
+          if (cudaStreamWaitEvent(p->stream, p->ev_w[i], 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
+        if ((s = pool_launch_retry(p, p->ops_dev + q, (int)(q2 - q), t))) return s;
+        for (int i = 0; i < nrun; ++i)
+          if (cudaStreamWaitEvent(p->stream, p->ev_r[i], 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
+        p->fused_ops += q2 - q;
+        p->warp_ops += q2 - q;
+      } else if (fused[q]) {
         const int cnt = (int)(q2 - q);
-        switch (p->kb) {
+        switch (bucket_of(q)) {
+          case 8: s = pool_launch<8>(p, p->ops_dev + q, cnt); break;
           case 16: s = pool_launch<16>(p, p->ops_dev + q, cnt); break;
           case 32: s = pool_launch<32>(p, p->ops_dev + q, cnt); break;
           default: s = pool_launch<64>(p, p->ops_dev + q, cnt); break;

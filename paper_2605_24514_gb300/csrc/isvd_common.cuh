@@ -40,18 +40,51 @@ struct DevState {
   unsigned int pad1;
 };
 
-// Optional phase timing of the core kernel (compile with -DISVD_CORE_TIMING): thread 0 stores
-// clock64() stamps into isvd_core_clock[0..15].
+// Optional phase timing (compile with -DISVD_CORE_TIMING): thread 0 of each CTA stores its
+// clock64() stamp i into isvd_core_clock[i] and adds it to isvd_core_clock_sum[i], so that for
+// many CTAs (sum[b] - sum[a]) / CTAs is the mean time between stamps a and b. Stamps 0-15 are
+// the core's, 16-31 the pool tick's.
 #ifdef ISVD_CORE_TIMING
-__device__ long long isvd_core_clock[16];
-#define ISVD_STAMP(i)                                                   \
-  do {                                                                  \
-    __syncthreads();                                                    \
-    if (threadIdx.x == 0) isvd_core_clock[(i)] = clock64();             \
+__device__ long long isvd_core_clock[32];
+__device__ unsigned long long isvd_core_clock_sum[32];
+#define ISVD_STAMP(i)                                                              \
+  do {                                                                             \
+    __syncthreads();                                                               \
+    if (threadIdx.x == 0) {                                                        \
+      const long long c_ = clock64();                                              \
+      isvd_core_clock[(i)] = c_;                                                   \
+      atomicAdd(&isvd_core_clock_sum[(i)], (unsigned long long)c_);               \
+    }                                                                              \
+  } while (0)
+// Warp-level phase timing: lane 0 adds the cycles since the warp's previous stamp to
+// isvd_core_clock_sum[i] and counts the hit in isvd_core_clock_cnt[i].
+__device__ unsigned long long isvd_core_clock_cnt[32];
+#define ISVD_WSTAMP_INIT(tp) long long tp = clock64()
+#define ISVD_WSTAMP(i, tp)                                                         \
+  do {                                                                             \
+    const long long c_ = clock64();                                                \
+    if ((threadIdx.x & 31) == 0) {                                                 \
+      atomicAdd(&isvd_core_clock_sum[(i)], (unsigned long long)(c_ - (tp)));       \
+      atomicAdd(&isvd_core_clock_cnt[(i)], 1ull);                                  \
+    }                                                                              \
+    (tp) = c_;                                                                     \
+  } while (0)
+#define ISVD_WCOUNT(i)                                                               \
+  do {                                                                               \
+    if ((threadIdx.x & 31) == 0) atomicAdd(&isvd_core_clock_cnt[(i)], 1ull);       \
   } while (0)
 #else
+#define ISVD_WCOUNT(i) \
+  do {                 \
+  } while (0)
 #define ISVD_STAMP(i) \
   do {                \
+  } while (0)
+#define ISVD_WSTAMP_INIT(tp) \
+  do {                       \
+  } while (0)
+#define ISVD_WSTAMP(i, tp) \
+  do {                     \
   } while (0)
 #endif
 

@@ -28,7 +28,11 @@ struct PoolOp {
 
 constexpr int kPoolZMax = 4096;  // longest projection side handled by the fused kernel
 
-__host__ __device__ constexpr int pool_threads(int kb) { return kb <= 16 ? 256 : kb <= 32 ? 288 : 544; }
+__host__ __device__ constexpr int pool_threads(int kb) {
+  return kb <= 8 ? 128 : kb <= 16 ? 256 : kb <= 32 ? 288 : 544;
+}
+// Rank bucket of the fused kernel for a stream of working-rank capacity k.
+__host__ __device__ constexpr int pool_bucket(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
 
 template <int KB>
 __host__ __device__ inline size_t pool_smem_bytes() {
@@ -58,6 +62,7 @@ template <int KB>
 __device__ void pool_project(const float* X, int ld, int64_t rows, const float* y, int r, double* red, double* out,
                              double* ysq_out) {
   constexpr int Q = (KB + 31) / 32;
+  constexpr int U4 = 4;  // rows in flight per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double acc[Q];
   float accs[Q];
@@ -69,16 +74,26 @@ __device__ void pool_project(const float* X, int ld, int64_t rows, const float* 
   float ysq = 0.f;
   double ysqd = 0.0;
   int run = 0;
-  for (int64_t row = warp; row < rows; row += nw) {
-    const float yv = y[row];
-    const float* xr = X + row * (int64_t)ld;
+  for (int64_t row0 = warp; row0 < rows; row0 += (int64_t)U4 * nw) {
+    float yv[U4], xv[U4][Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int c = lane + 32 * q;
-      if (c < r) accs[q] = fmaf(xr[c], yv, accs[q]);
+    for (int u = 0; u < U4; ++u) {  // issue every load of the group first
+      const int64_t row = row0 + (int64_t)u * nw;
+      const bool ok = row < rows;
+      yv[u] = ok ? y[row] : 0.f;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int c = lane + 32 * q;
+        xv[u][q] = (ok && c < r) ? X[row * (int64_t)ld + c] : 0.f;
+      }
     }
-    ysq = fmaf(yv, yv, ysq);
-    if (++run == 8) {
+#pragma unroll
+    for (int u = 0; u < U4; ++u) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) accs[q] = fmaf(xv[u][q], yv[u], accs[q]);
+      ysq = fmaf(yv[u], yv[u], ysq);
+    }
+    if (++run == 2) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         acc[q] += (double)accs[q];
@@ -113,7 +128,7 @@ __device__ void pool_project(const float* X, int ld, int64_t rows, const float* 
 template <int KB>
 __device__ void pool_rotate(float* X, int ld, int64_t rows, const float* R, int ldr, int c_in, int k_out,
                             const float* zsrc, const float* p2f, float inv_rho, bool newrow) {
-  constexpr int HALF = KB <= 32 ? KB : KB / 2;  // outputs per pass
+  constexpr int HALF = KB <= 16 ? KB : 16;  // outputs per pass (bounds the live registers)
   for (int64_t row = threadIdx.x; row < rows; row += blockDim.x) {
     float* xr = X + row * (int64_t)ld;
     float xv[KB];
@@ -142,12 +157,13 @@ __device__ void pool_rotate(float* X, int ld, int64_t rows, const float* R, int 
       float o[HALF];
 #pragma unroll
       for (int jj = 0; jj < HALF; ++jj) o[jj] = 0.f;
-#pragma unroll 4
-      for (int c = 0; c < c_in; ++c) {
-        const float xc = xv[c < KB ? c : 0];
-        const float* rr = R + (size_t)c * ldr + h0;
 #pragma unroll
-        for (int jj = 0; jj < HALF; ++jj) o[jj] = fmaf(xc, rr[jj], o[jj]);
+      for (int c = 0; c < KB; ++c) {
+        if (c < c_in) {
+          const float* rr = R + (size_t)c * ldr + h0;
+#pragma unroll
+          for (int jj = 0; jj < HALF; ++jj) o[jj] = fmaf(xv[c], rr[jj], o[jj]);
+        }
       }
       if (zsrc) {
         const float* rr = R + (size_t)c_in * ldr + h0;
@@ -171,10 +187,14 @@ __device__ void pool_rotate(float* X, int ld, int64_t rows, const float* R, int 
   }
 }
 
+// Resident CTAs per SM the register budget is shaped for.
+__host__ __device__ constexpr int pool_min_blocks(int kb) { return kb <= 8 ? 6 : kb <= 16 ? 4 : kb <= 32 ? 3 : 1; }
+
+// One whole update of one stream by the calling CTA (blockDim = pool_threads(KB), dynamic shared
+// memory pool_smem_bytes<KB>()).
 template <int KB>
-__global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __restrict__ ops) {
+__device__ void pool_tick_body(const PoolOp& op) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const PoolOp op = ops[blockIdx.x];
   const int t = threadIdx.x;
   const int nw = blockDim.x >> 5;
   size_t core_b = core_fast_smem_bytes<float>(KB);
@@ -194,6 +214,7 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
   DevState* st = op.st;
   const int r = st->r;
   const int kind = op.kind;
+  ISVD_STAMP(16);
   // Projection side: V for a row append, U for a column append.
   float* Xp = kind == kRow ? op.V : op.U;
   const int64_t prow = kind == kRow ? op.n : op.m;
@@ -206,6 +227,7 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
     }
     // Pass 1: p1 = X^T x, ||x||^2.
     pool_project<KB>(Xp, op.ld, prow, op.x, r, red, p1, &s_sc[0]);
+    ISVD_STAMP(17);
     // Pass 2: z1 = x - X p1 per row (float-float, one thread per row) into zbuf, ||z1||^2.
     float* p1h = reinterpret_cast<float*>(red);  // p1 as float pairs (red is free now)
     float* p1l = p1h + (KB + 2);
@@ -218,12 +240,27 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
     ff zn{0.f, 0.f};
     for (int64_t row = t; row < prow; row += blockDim.x) {
       const float* xr = Xp + row * (int64_t)op.ld;
+      float xv[KB];  // the row, loaded with vector loads before any arithmetic
+#pragma unroll
+      for (int c4 = 0; c4 < KB; c4 += 4) {
+        if (c4 < r) {
+          const float4 v = *reinterpret_cast<const float4*>(xr + c4);
+          xv[c4] = v.x;
+          xv[c4 + 1] = v.y;
+          xv[c4 + 2] = v.z;
+          xv[c4 + 3] = v.w;
+        } else {
+          xv[c4] = xv[c4 + 1] = xv[c4 + 2] = xv[c4 + 3] = 0.f;
+        }
+      }
       ff s{op.x[row], 0.f};
-      for (int c = 0; c < r; ++c) {
-        const float v = xr[c];
-        ff pr = two_prod(v, p1h[c]);
-        pr.lo = fmaf(v, p1l[c], pr.lo);
-        s = ff_add(s, ff{-pr.hi, -pr.lo});
+#pragma unroll
+      for (int c = 0; c < KB; ++c) {
+        if (c < r) {
+          ff pr = two_prod(xv[c], p1h[c]);
+          pr.lo = fmaf(xv[c], p1l[c], pr.lo);
+          s = ff_add(s, ff{-pr.hi, -pr.lo});
+        }
       }
       zbuf[row] = s.hi + s.lo;
       zn = ff_add(zn, ff_sqr(s));
@@ -239,6 +276,7 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
       s_sc[1] = s;
     }
     __syncthreads();
+    ISVD_STAMP(18);
     // Pass 3 (CGS2): p2 = X^T z1; p = p1 + p2; rho^2 = ||z1||^2 - ||p2||^2.
     pool_project<KB>(Xp, op.ld, prow, zbuf, r, red, p2, nullptr);
     if (t < 32) {
@@ -277,6 +315,7 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
     }
     __syncthreads();
   }
+  ISVD_STAMP(19);
   // Core SVD into shared memory.
   CoreIn in;
   in.kind = kind;
@@ -296,12 +335,16 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
   if (k_out < 0) k_out = core_svd_cta<float, float>(in, core_smem, UKs, VKs, KB, op.sig, &s_sweeps);
   __syncthreads();
   const bool grew = kind != kEntry && in.grew;
-  const float inv_rho = grew ? (float)(1.0 / st->rho) : 0.f;
+  __shared__ float s_inv_rho;
+  if (t == 0) s_inv_rho = grew ? (float)(1.0 / st->rho) : 0.f;
   __syncthreads();
+  const float inv_rho = s_inv_rho;
+  ISVD_STAMP(20);
   // Rotations (Step 3): row append U <- [U; 0] U_K + new row, V <- V V_K + z_hat V_K[r];
   // column append swaps the roles; entry: U <- U U_K, V <- V V_K.
   if (kind == kRow) {
     pool_rotate<KB>(op.U, op.ld, op.m, UKs, KB, r, k_out, nullptr, nullptr, 0.f, true);
+    ISVD_STAMP(21);
     pool_rotate<KB>(op.V, op.ld, op.n, VKs, KB, r, k_out, grew ? zbuf : nullptr, p2f, inv_rho, false);
   } else if (kind == kCol) {
     pool_rotate<KB>(op.U, op.ld, op.m, VKs, KB, r, k_out, grew ? zbuf : nullptr, p2f, inv_rho, false);
@@ -311,12 +354,33 @@ __global__ void __launch_bounds__(pool_threads(KB)) k_pool_tick(const PoolOp* __
     pool_rotate<KB>(op.V, op.ld, op.n, VKs, KB, r, k_out, nullptr, nullptr, 0.f, false);
   }
   __syncthreads();
+  ISVD_STAMP(22);
   if (t == 0) {
     st->r_in = r;
     st->k_out = k_out;
     st->r = k_out;
     st->sweeps = s_sweeps;
     if (s_sweeps < 0) atomicOr(&st->status, kStNotConv);
+  }
+}
+
+template <int KB>
+__global__ void __launch_bounds__(pool_threads(KB), pool_min_blocks(KB)) k_pool_tick(const PoolOp* __restrict__ ops) {
+  const PoolOp op = ops[blockIdx.x];
+  pool_tick_body<KB>(op);
+}
+
+// The updates listed in retry[0 .. *retry_n) (indices into ops), one at a time per block. Rare, so
+// it is not shaped for occupancy (one block per SM, registers unconstrained).
+template <int KB>
+__global__ void __launch_bounds__(pool_threads(KB), 1)
+    k_pool_retry(const PoolOp* __restrict__ ops, const int* __restrict__ retry, const int* __restrict__ retry_n) {
+  const int n = *retry_n;
+#pragma unroll 1
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    const PoolOp op = ops[retry[b]];
+    pool_tick_body<KB>(op);
+    __syncthreads();
   }
 }
 

@@ -1,0 +1,573 @@
+// Batched row and column appends (Section 2.2) with ONE WARP per stream update, for streams of
+// working-rank capacity up to 32.
+//
+// The CTA-per-update kernel (pool_kernels.cuh) spends most of its time in block barriers and in
+// serial rounds of dependent loads, while its SM is shared with other CTAs doing the same. A warp
+// holds everything an update of rank <= 32 needs: the projection side's rows stream through the
+// lanes (one row per lane, a whole row in registers), reductions over rows are register
+// transposes by shuffles, and the core - a rank-one modification of a diagonal matrix - is solved
+// root-per-lane. There are no block barriers and the streams of a tick run in about one wave;
+// one launch per rank bucket (8, 16, 32) keeps each kernel's code small enough for the
+// instruction caches.
+//
+// Per update (P = the projection side: V for a row append, U for a column append; Q = the other
+// side; x = the new row or column):
+//   pass 1      p1 = P^T x, ||x||^2                       (FP32 products, float-float ||x||^2)
+//   pass 2      z1 = x - P p1 (float-float per row), p2 = P^T z1, ||z1||^2     (CGS2, one read)
+//               p = p1 + p2, rho^2 = ||z1||^2 - ||p2||^2, grew = rho > tol_rel ||x||
+//   core        K = [[Sigma, 0], [p, rho]]: K^T K = diag(sigma^2, 0) + w w^T with w = (p, rho);
+//               secular roots (one per lane, near-pole rational iteration with a bisection
+//               safeguard, poles as float pairs), corrected weights w_hat (Gu-Eisenstat), and
+//               both vector sets in closed form from w_hat (see ge_append_vectors); singular
+//               values sqrt(lambda) in FP64
+//   rotations   P' = [P z_hat] V_K with z_hat = (x - P p) / rho recomputed per row in float-float,
+//               Q' = blkdiag(Q, 1) U_K (the new row of Q' is U_K's last row): a separate
+//               row-parallel launch (k_pool_rotate, one thread per row) reading V_K, U_K and p
+//               from a per-update scratch record, since one warp cannot hide the latency of
+//               rotating hundreds of rows.
+// An update the warp cannot finish on this path (non-finite input, coinciding poles, a deflated
+// rho pole, a rejected weight correction, an empty factorisation) changes nothing and is listed
+// for the CTA kernel (k_pool_retry), which has the Jacobi fallback.
+#pragma once
+
+#include "core_fast.cuh"
+#include "isvd_common.cuh"
+#include "pool_kernels.cuh"
+
+namespace isvd {
+
+constexpr int kWarpKB = 32;         // largest rank bucket of the warp kernel
+constexpr int kWarpsPerBlock = 4;   // independent warps per block (no block-level sync)
+
+// Per-warp shared memory for rank bucket KB.
+template <int KB>
+struct alignas(16) WarpSmem {
+  float RP[(KB + 1) * 32];  // V_K for P: row c (original order; row r = z_hat's), column jj, stride KB;
+                            // during the root search, each lane's shifted poles (pole i at i * 32 + lane)
+  float RQ[(KB + 1) * KB];  // U_K for Q: row c (row r = the new row), column jj, stride KB
+  float dhi[KB + 1], dlo[KB + 1];  // ascending poles as float pairs
+  float w[KB + 1];                 // weights in pole order
+  float tau[KB + 1];               // root j = pole org[j] + tau[j]
+  float lhi[KB + 1], llo[KB + 1];  // roots as float pairs
+  float what[KB + 1];              // w^2 during the root search, then the corrected weights
+  float ph[KB], pl[KB];            // p as float pairs (original order)
+  float sf[KB];                    // sigma (float, original order)
+  int org[KB + 1], row[KB + 1], perm[KB + 1];
+};
+
+template <int KB>
+constexpr size_t warp_block_smem() {
+  return sizeof(WarpSmem<KB>) * kWarpsPerBlock;
+}
+
+// What the warp kernel hands to the rotation kernel for one update (global scratch).
+template <int KB>
+struct alignas(16) RotScratch {
+  float RP[(KB + 1) * KB];  // V_K (row stride KB), row r = z_hat's when the rank grew
+  float RQ[(KB + 1) * KB];  // U_K (row stride KB)
+  float ph[KB], pl[KB];     // p as float pairs
+  float inv_rho;
+  int r, k_out, grew;       // k_out < 0: the update was handed to the CTA kernel
+};
+constexpr size_t kRotScratchStride = sizeof(RotScratch<kWarpKB>);  // bytes per update slot
+
+// r leading entries of a row (16-byte aligned, row stride a multiple of 4 floats), zero beyond.
+template <int KB>
+__device__ __forceinline__ void warp_load_row(const float* p, int r, float (&v)[KB]) {
+#pragma unroll
+  for (int c4 = 0; c4 < KB; c4 += 4) {
+    if (c4 < r) {
+      const float4 q = *reinterpret_cast<const float4*>(p + c4);
+      v[c4] = q.x;
+      v[c4 + 1] = c4 + 1 < r ? q.y : 0.f;
+      v[c4 + 2] = c4 + 2 < r ? q.z : 0.f;
+      v[c4 + 3] = c4 + 3 < r ? q.w : 0.f;
+    } else {
+      v[c4] = v[c4 + 1] = v[c4 + 2] = v[c4 + 3] = 0.f;
+    }
+  }
+}
+
+// Warp-wide sums of KB per-lane vectors: returns, on lane L, sum over lanes of v[L % KB]. The
+// first log2(KB) rounds exchange half of the remaining entries with the partner lane (a register
+// transpose, KB - 1 shuffles), the rest add across lane groups.
+template <int KB>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[KB], int lane) {
+#pragma unroll
+  for (int o = KB / 2; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float s = v[0];
+#pragma unroll
+  for (int o = KB; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// out[jj] = sum_{c < r} xv[c] R[c][jj] (+ zh R[r][jj]) for jj < k_out (R row stride KB), written
+// back to row y, eight output columns per pass (the pass loop stays rolled: compact code).
+template <int KB>
+__device__ __forceinline__ void warp_rotate_row(float* y, const float (&xv)[KB], int r, const float* R, int k_out,
+                                                float zh, bool withz) {
+#pragma unroll 1
+  for (int h0 = 0; h0 < k_out; h0 += 8) {
+    float o[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) o[jj] = 0.f;
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c < r) {
+        const float4* rr = reinterpret_cast<const float4*>(R + c * KB + h0);
+        const float4 a = rr[0], b = rr[1];
+        o[0] = fmaf(xv[c], a.x, o[0]);
+        o[1] = fmaf(xv[c], a.y, o[1]);
+        o[2] = fmaf(xv[c], a.z, o[2]);
+        o[3] = fmaf(xv[c], a.w, o[3]);
+        o[4] = fmaf(xv[c], b.x, o[4]);
+        o[5] = fmaf(xv[c], b.y, o[5]);
+        o[6] = fmaf(xv[c], b.z, o[6]);
+        o[7] = fmaf(xv[c], b.w, o[7]);
+      }
+    }
+    if (withz) {
+      const float4* rr = reinterpret_cast<const float4*>(R + r * KB + h0);
+      const float4 a = rr[0], b = rr[1];
+      o[0] = fmaf(zh, a.x, o[0]);
+      o[1] = fmaf(zh, a.y, o[1]);
+      o[2] = fmaf(zh, a.z, o[2]);
+      o[3] = fmaf(zh, a.w, o[3]);
+      o[4] = fmaf(zh, b.x, o[4]);
+      o[5] = fmaf(zh, b.y, o[5]);
+      o[6] = fmaf(zh, b.z, o[6]);
+      o[7] = fmaf(zh, b.w, o[7]);
+    }
+    if (h0 + 7 < k_out) {
+      *reinterpret_cast<float4*>(y + h0) = make_float4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<float4*>(y + h0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (h0 + jj < k_out) y[h0 + jj] = o[jj];
+    }
+  }
+}
+
+// Next non-deflated pole above j (bit set in mask), or -1.
+__device__ __forceinline__ int warp_next_pole(uint64_t mask, int j) {
+  const uint64_t m = j + 1 < 64 ? (mask >> (j + 1)) : 0ull;
+  return m ? j + __ffsll((long long)m) : -1;
+}
+
+// One row or column append of one stream by the calling warp. Returns false, with nothing
+// written, when the update has to take the CTA kernel instead.
+template <int KB>
+__device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& RS) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  DevState* st = op.st;
+  const int r = st->r;
+  const int kt = st->k;
+  const bool is_row = op.kind == kRow;
+  float* P = is_row ? op.V : op.U;
+  float* Q = is_row ? op.U : op.V;
+  const int64_t nP = is_row ? op.n : op.m;
+  const int64_t nQ = is_row ? op.m : op.n;
+  const int64_t ld = op.ld;
+  const float* x = op.x;
+  if (r < 1 || r > KB) return false;
+  ISVD_WSTAMP_INIT(tp);
+
+  // Pass 1: p1 = P^T x and ||x||^2.
+  float acc[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
+  ff xx{0.f, 0.f};
+  for (int64_t row = lane; row < nP; row += 32) {
+    float pv[KB];
+    warp_load_row<KB>(P + row * ld, r, pv);
+    const float xv = x[row];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[c] = fmaf(pv[c], xv, acc[c]);
+    xx = ff_add(xx, two_prod(xv, xv));
+  }
+  const float p1c = warp_transpose_sum<KB>(acc, lane);  // p1[lane % KB]
+  xx = ff_group_sum<32>(xx);
+  if (lane < KB) S.ph[lane] = lane < r ? p1c : 0.f;
+  __syncwarp();
+  ISVD_WSTAMP(17, tp);
+
+  // Pass 2 (CGS2): z1 = x - P p1 per row in float-float, p2 = P^T z1, ||z1||^2.
+#pragma unroll
+  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
+  ff zz{0.f, 0.f};
+  for (int64_t row = lane; row < nP; row += 32) {
+    float pv[KB];
+    warp_load_row<KB>(P + row * ld, r, pv);
+    ff s{x[row], 0.f};
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c < r) {
+        const ff pr = two_prod(pv[c], S.ph[c]);
+        s = ff_add(s, ff{-pr.hi, -pr.lo});
+      }
+    }
+    const float z1 = s.hi + s.lo;
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[c] = fmaf(pv[c], z1, acc[c]);
+    zz = ff_add(zz, ff_sqr(s));
+  }
+  const float p2c = warp_transpose_sum<KB>(acc, lane);  // p2[lane % KB]
+  zz = ff_group_sum<32>(zz);
+  double pn = (lane < KB && lane < r) ? (double)p2c * (double)p2c : 0.0;
+  pn = warp_sum(pn);
+  const double xn2 = (double)xx.hi + (double)xx.lo;
+  const double rho2 = ((double)zz.hi + (double)zz.lo) - pn;
+  ISVD_WSTAMP(18, tp);
+  if (!isfinite(xn2) || !isfinite(rho2)) {
+    ISVD_WCOUNT(25);
+    return false;
+  }
+  const double rho = sqrt(fmax(rho2, 0.0));
+  const double xnorm = sqrt(xn2);
+  const bool grew = rho > op.tol_rel * xnorm;
+  __syncwarp();
+  if (lane < KB) {
+    float hi, lo;
+    two_sum(p1c, p2c, hi, lo);
+    S.ph[lane] = lane < r ? hi : 0.f;
+    S.pl[lane] = lane < r ? lo : 0.f;
+  }
+  __syncwarp();
+
+  // Core setup: ascending poles (0 with weight rho when the rank grows), sigma_{r-1}^2 .. sigma_0^2.
+  const int nc = grew ? r + 1 : r;
+  const int off = grew ? 1 : 0;
+  for (int s_ = lane; s_ < nc; s_ += 32) {
+    if (grew && s_ == 0) {
+      S.dhi[0] = 0.f;
+      S.dlo[0] = 0.f;
+      S.w[0] = (float)rho;
+      S.row[0] = r;
+    } else {
+      const int i = r - 1 - (s_ - off);
+      const double sg = op.sig[i];
+      const ff d2 = ff_of(sg * sg);
+      S.dhi[s_] = d2.hi;
+      S.dlo[s_] = d2.lo;
+      S.w[s_] = S.ph[i] + S.pl[i];
+      S.row[s_] = i;
+    }
+  }
+  for (int i = lane; i < r; i += 32) S.sf[i] = (float)op.sig[i];
+  __syncwarp();
+  ff wq{0.f, 0.f};
+  for (int s_ = lane; s_ < nc; s_ += 32) wq = ff_add(wq, two_prod(S.w[s_], S.w[s_]));
+  wq = ff_group_sum<32>(wq);
+  const float wn2 = wq.hi + wq.lo;
+  const float thr = 1e-7f * sqrtf(wn2);  // deflation: |w_j| <= thr counts as zero
+  const float dscale = fmaxf(fabsf(S.dhi[0]), fabsf(S.dhi[nc - 1]));
+  const bool nd0 = lane < nc && fabsf(S.w[lane]) > thr;
+  const bool nd1 = lane + 32 < nc && fabsf(S.w[lane + 32]) > thr;
+  const uint64_t mask = (uint64_t)__ballot_sync(kFull, nd0) | ((uint64_t)__ballot_sync(kFull, nd1) << 32);
+  int bad = 0;
+  float ws = 0.f;
+  for (int j = lane; j < nc; j += 32) {
+    const ff dj{S.dhi[j], S.dlo[j]};
+    if (j + 1 < nc && ff_sub_to_f(ff{S.dhi[j + 1], S.dlo[j + 1]}, dj) < 0.f) bad |= 1;  // order
+    if ((mask >> j) & 1ull) {
+      const int nx = warp_next_pole(mask, j);
+      if (nx >= 0 && ff_sub_to_f(ff{S.dhi[nx], S.dlo[nx]}, dj) <= kTieRel * dscale) bad |= 2;  // ties
+      ws += S.w[j] * S.w[j];
+      S.what[j] = S.w[j] * S.w[j];
+    } else {
+      S.what[j] = 0.f;
+    }
+  }
+  if (grew && !(mask & 1ull)) bad |= 4;  // deflated rho pole
+  if (mask == 0ull) bad |= 8;
+  ws = warp_sum(ws) * (1.f + 1e-5f);
+  bad = __reduce_or_sync(kFull, bad);
+  if (bad) {
+    if (bad & 1) ISVD_WCOUNT(26);
+    if (bad & 2) ISVD_WCOUNT(27);
+    if (bad & 4) ISVD_WCOUNT(28);
+    if (bad & 8) ISVD_WCOUNT(29);
+    return false;
+  }
+  __syncwarp();
+  ISVD_WSTAMP(19, tp);
+
+  // Roots, one per lane: lambda_j in (d_j, d_next) (the last one in (d_last, d_last + ||w||^2)),
+  // in the offset u from the nearer pole. The lane's poles shifted to the origin live in RP
+  // (column = lane) while it searches.
+  float* sh = S.RP;
+  for (int j = lane; j < nc; j += 32) {
+    if (!((mask >> j) & 1ull)) {
+      S.tau[j] = 0.f;
+      S.org[j] = j;
+      S.lhi[j] = S.dhi[j];
+      S.llo[j] = S.dlo[j];
+      continue;
+    }
+    const int nx = warp_next_pole(mask, j);
+    const bool last = nx < 0;
+    const ff lo{S.dhi[j], S.dlo[j]};
+    const ff hi = last ? lo : ff{S.dhi[nx], S.dlo[nx]};
+    const float width = last ? ws : ff_sub_to_f(hi, lo);
+    const float half = 0.5f * width;
+    float fm = 1.f;
+    for (int i = 0; i < nc; ++i) {
+      const float di = S.what[i] > 0.f ? ff_sub_to_f(ff{S.dhi[i], S.dlo[i]}, lo) : 1e30f;
+      sh[i * 32 + lane] = di;
+      fm += __fdividef(S.what[i], di - half);
+    }
+    float sgn = 1.f, b = last ? width : half;
+    int o = j;
+    if (!last && !(fm > 0.f)) {
+      sgn = -1.f;
+      b = half;
+      o = nx;
+      for (int i = 0; i < nc; ++i)
+        sh[i * 32 + lane] = S.what[i] > 0.f ? ff_sub_to_f(ff{S.dhi[i], S.dlo[i]}, hi) : 1e30f;
+    }
+    // h(u) = sgn f(sgn u) rises from -inf at the near pole (u = 0); each step fits
+    // h ~ C - S/u to h and h' at u and takes its root, or bisects (geometrically across decades).
+    float a = 0.f, u = 0.5f * b;
+    for (int it = 0; it < 40; ++it) {
+      const float tk = sgn * u;
+      float fs = 0.f, ds = 0.f;
+      for (int i = 0; i < nc; ++i) {
+        const float rq = __fdividef(1.f, sh[i * 32 + lane] - tk);
+        const float t1 = S.what[i] * rq;
+        fs += t1;
+        ds = fmaf(t1, rq, ds);
+      }
+      const float h = sgn * (1.f + fs);
+      if (h == 0.f) break;
+      if (h < 0.f) a = u;
+      else b = u;
+      const float C = h + ds * u;
+      float un = (C > 0.f) ? ds * u * u / C : -1.f;
+      if (!(un > a && un < b)) un = (a > 0.f && b > 4.f * a) ? sqrtf(a) * sqrtf(b) : 0.5f * (a + b);
+      const bool done = fabsf(un - u) <= 1e-7f * un || (b - a) <= 2.4e-7f * b;
+      u = un;
+      if (done) break;
+    }
+    const float tau = sgn * u;
+    const ff og{S.dhi[o], S.dlo[o]};
+    const ff lam = ff_add(og, ff{tau, 0.f});
+    S.tau[j] = tau;
+    S.org[j] = o;
+    S.lhi[j] = lam.hi;
+    S.llo[j] = lam.lo;
+  }
+  __syncwarp();
+  ISVD_WSTAMP(20, tp);
+
+  // Corrected weights: w_hat_i^2 = prod_j (lambda_j - d_i) / prod_{l != i} (d_l - d_i), each
+  // root paired with its neighbouring pole; rejected when |w_hat - w| > kGeTolEps eps ||w||.
+  const float tol = kGeTolEps * Eps<float>::v * sqrtf(wn2);
+  int badge = 0;
+  for (int i = lane; i < nc; i += 32) {
+    float wh = 0.f;
+    if ((mask >> i) & 1ull) {
+      const ff di{S.dhi[i], S.dlo[i]};
+      float prod = 1.f;
+      for (int j = 0; j < nc; ++j) {
+        if (!((mask >> j) & 1ull)) continue;
+        const int o = S.org[j];
+        const float num = ff_sub_to_f(ff{S.dhi[o], S.dlo[o]}, di) + S.tau[j];
+        const int nj = warp_next_pole(mask, j);
+        if (nj < 0) {
+          prod *= num;
+        } else {
+          const int pj = j < i ? j : nj;
+          prod *= __fdividef(num, ff_sub_to_f(ff{S.dhi[pj], S.dlo[pj]}, di));
+        }
+      }
+      wh = copysignf(sqrtf(fmaxf(prod, 0.f)), S.w[i]);
+      if (!(fabsf(wh - S.w[i]) <= tol)) badge = 1;
+    }
+    S.what[i] = wh;
+  }
+  if (__any_sync(kFull, badge)) {
+    ISVD_WCOUNT(30);
+    return false;
+  }
+
+  // Descending order of the roots (compared as float pairs, ties by index).
+  for (int j = lane; j < nc; j += 32) {
+    const float hj = S.lhi[j], lj = S.llo[j];
+    int rk = 0;
+    for (int l = 0; l < nc; ++l) {
+      const float hl = S.lhi[l], ll = S.llo[l];
+      rk += (hl > hj) || (hl == hj && (ll > lj || (ll == lj && l < j)));
+    }
+    S.perm[rk] = j;
+  }
+  __syncwarp();
+  const int k_out = kt < nc ? kt : nc;
+  ISVD_WSTAMP(21, tp);
+
+  // Vectors of output column jj = lane: v_j = (w_hat_i / (d_i - lambda_j))_i / norm into RP,
+  // u_j = (sigma_i v_ji ; -1) / norm into RQ; a deflated pole keeps e_j on both sides.
+  if (lane < k_out) {
+    const int jj = lane, j = S.perm[jj];
+    if (!((mask >> j) & 1ull)) {
+      const int cj = S.row[j];
+      for (int c = 0; c < nc; ++c) S.RP[c * KB + jj] = c == cj ? 1.f : 0.f;
+      for (int c = 0; c <= r; ++c) S.RQ[c * KB + jj] = c == cj ? 1.f : 0.f;
+    } else {
+      const int o = S.org[j];
+      const ff dor{S.dhi[o], S.dlo[o]};
+      const float tj = S.tau[j];
+      float sv = 0.f, su = 0.f;
+      for (int i = 0; i < nc; ++i) {
+        const int c = S.row[i];
+        const float wh = S.what[i];
+        const float v = wh != 0.f ? -wh / (ff_sub_to_f(dor, ff{S.dhi[i], S.dlo[i]}) + tj) : 0.f;
+        S.RP[c * KB + jj] = v;
+        sv = fmaf(v, v, sv);
+        if (c < r) {
+          const float uv = S.sf[c] * v;
+          su = fmaf(uv, uv, su);
+        }
+      }
+      const float iv = rsqrtf(sv), iu = rsqrtf(su + 1.f);
+      for (int c = 0; c < nc; ++c) {
+        const float v = S.RP[c * KB + jj];
+        if (c < r) S.RQ[c * KB + jj] = S.sf[c] * v * iu;
+        S.RP[c * KB + jj] = v * iv;
+      }
+      S.RQ[r * KB + jj] = -iu;
+    }
+    op.sig[jj] = sqrt((double)S.lhi[j] + (double)S.llo[j]);
+  }
+  __syncwarp();
+
+  ISVD_WSTAMP(22, tp);
+  // Hand V_K, U_K and p to the rotation kernel; the new row of Q is U_K's last row.
+  for (int idx = lane; idx < (r + 1) * KB; idx += 32) {
+    RS.RP[idx] = S.RP[idx];
+    RS.RQ[idx] = S.RQ[idx];
+  }
+  for (int c = lane; c < r; c += 32) {
+    RS.ph[c] = S.ph[c];
+    RS.pl[c] = S.pl[c];
+  }
+  if (lane == 0) {
+    RS.inv_rho = grew ? (float)(1.0 / rho) : 0.f;
+    RS.r = r;
+    RS.k_out = k_out;
+    RS.grew = grew ? 1 : 0;
+  }
+  if (lane < k_out) Q[nQ * ld + lane] = S.RQ[r * KB + lane];
+  // The dense matrix gains x as its new row / column.
+  for (int64_t c = lane; c < nP; c += 32) {
+    if (is_row) op.A[op.m * op.lda + c] = x[c];
+    else op.A[c * op.lda + op.n] = x[c];
+  }
+  if (lane == 0) {
+    st->rho = rho;
+    st->grew = grew ? 1 : 0;
+    st->novelty = xnorm > 0.0 ? rho / xnorm : 0.0;
+    st->xnorm2 = xn2;
+    st->N += xn2;
+    st->r_in = r;
+    st->k_out = k_out;
+    st->r = k_out;
+    st->sweeps = 102;
+  }
+  ISVD_WSTAMP(23, tp);
+  return true;
+}
+
+// ops[0 .. count): row/column appends of streams in rank bucket KB, one warp each. Updates that
+// need the CTA kernel are listed in retry[] as base + index (count in *retry_n), untouched.
+// Also fills block_op[chunk_start[e] + i] = e for the update's rotation blocks.
+constexpr int kPoolRotRows = 128;
+template <int KB>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 8 ? 8 : KB <= 16 ? 6 : 5)
+    k_pool_warp(const PoolOp* __restrict__ ops, int count, int base, int* __restrict__ retry,
+                int* __restrict__ retry_n, RotScratch<KB>* __restrict__ scratch, const int* __restrict__ chunk_start,
+                int* __restrict__ block_op) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wid = threadIdx.x >> 5;
+  const int e = blockIdx.x * kWarpsPerBlock + wid;
+  if (e >= count) return;
+  WarpSmem<KB>& S = reinterpret_cast<WarpSmem<KB>*>(smem)[wid];
+  const PoolOp op = ops[e];
+  {
+    const int64_t nP = op.kind == kRow ? op.n : op.m, nQ = op.kind == kRow ? op.m : op.n;
+    const int nb = (int)((nP + kPoolRotRows - 1) / kPoolRotRows + (nQ + kPoolRotRows - 1) / kPoolRotRows);
+    const int c0 = chunk_start[e];
+    for (int i = threadIdx.x & 31; i < nb; i += 32) block_op[c0 + i] = e;
+  }
+  const bool ok = warp_append<KB>(op, S, scratch[e]);
+  if (!ok && (threadIdx.x & 31) == 0) {
+    scratch[e].k_out = -1;
+    retry[atomicAdd(retry_n, 1)] = base + e;
+  }
+}
+
+// Rotations of the warp kernel's updates: block b rotates 128 rows of one side of update
+// e = block_op[b] (chunk_start[e] = its first block; per update ceil(nP / 128) blocks for the
+// projection side, then ceil(nQ / 128) for the other), one thread per row, V_K or U_K in shared
+// memory.
+template <int KB>
+__global__ void __launch_bounds__(kPoolRotRows) k_pool_rotate(const PoolOp* __restrict__ ops,
+                                                              const RotScratch<KB>* __restrict__ scratch,
+                                                              const int* __restrict__ chunk_start,
+                                                              const int* __restrict__ block_op) {
+  __shared__ __align__(16) float R[(KB + 1) * KB];
+  __shared__ float ph[KB], pl[KB];
+  const int b = blockIdx.x;
+  const int e = block_op[b];
+  const RotScratch<KB>& sc = scratch[e];
+  const int k_out = sc.k_out;
+  if (k_out < 0) return;
+  const PoolOp& op = ops[e];
+  const bool is_row = op.kind == kRow;
+  const int64_t nP = is_row ? op.n : op.m;
+  const int64_t nQ = is_row ? op.m : op.n;
+  const int cP = (int)((nP + kPoolRotRows - 1) / kPoolRotRows);
+  const int ci = b - chunk_start[e];
+  const bool pside = ci < cP;
+  const int r = sc.r;
+  const bool withz = pside && sc.grew;
+  const float* src = pside ? sc.RP : sc.RQ;
+  for (int idx = threadIdx.x; idx < (r + 1) * KB; idx += kPoolRotRows) R[idx] = src[idx];
+  if (withz)
+    for (int c = threadIdx.x; c < r; c += kPoolRotRows) {
+      ph[c] = sc.ph[c];
+      pl[c] = sc.pl[c];
+    }
+  __syncthreads();
+  const int64_t row = (int64_t)(pside ? ci : ci - cP) * kPoolRotRows + threadIdx.x;
+  if (row >= (pside ? nP : nQ)) return;
+  float* X = pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V);
+  float* xr = X + row * (int64_t)op.ld;
+  float xv[KB];
+  warp_load_row<KB>(xr, r, xv);
+  float zh = 0.f;
+  if (withz) {
+    ff s{op.x[row], 0.f};
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c < r) {
+        ff q = two_prod(xv[c], ph[c]);
+        q.lo = fmaf(xv[c], pl[c], q.lo);
+        s = ff_add(s, ff{-q.hi, -q.lo});
+      }
+    }
+    zh = (s.hi + s.lo) * sc.inv_rho;
+  }
+  warp_rotate_row<KB>(xr, xv, r, R, k_out, zh, withz);
+}
+
+}  // namespace isvd

@@ -7,11 +7,12 @@
 namespace isvd {
 
 // C[a, b] += sum_row X[row, a] * Y[row, b] for a < cx, b < cy (C row-major FP64, ldc), over a
-// slice of rows per block (grid.z). Products are summed in T over runs of 16 rows, then in FP64.
+// slice of rows per block (grid.z). Products are summed in T over runs of 16 rows, then in FP64;
+// with kExact every product is formed and summed in FP64 (exact products of FP32 data).
 // 32 x 32 output tile per block, 256 threads, 4 outputs per thread.
 constexpr int kTnTile = 32;
 constexpr int kTnChunk = 64;
-template <typename T>
+template <typename T, bool kExact = false>
 __global__ void __launch_bounds__(256) k_gemm_tn(const T* __restrict__ X, int64_t ldx, int cx, const T* __restrict__ Y,
                                                  int64_t ldy, int cy, int64_t rows, int64_t rows_per_split,
                                                  double* __restrict__ C, int64_t ldc) {
@@ -33,17 +34,26 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const T* __restrict__ X, int64_
       ys[rr][c] = (okr && b0 + c < cy) ? Y[row * ldy + b0 + c] : T(0);
     }
     __syncthreads();
-    T part[4] = {0, 0, 0, 0};
+    if constexpr (kExact) {
 #pragma unroll 4
-    for (int rr = 0; rr < kTnChunk; ++rr) {
-      const T xv = xs[rr][ta];
+      for (int rr = 0; rr < kTnChunk; ++rr) {
+        const double xv = (double)xs[rr][ta];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) part[q] += xv * ys[rr][tb + 8 * q];
-      if ((rr & 15) == 15) {
+        for (int q = 0; q < 4; ++q) acc[q] = fma(xv, (double)ys[rr][tb + 8 * q], acc[q]);
+      }
+    } else {
+      T part[4] = {0, 0, 0, 0};
+#pragma unroll 4
+      for (int rr = 0; rr < kTnChunk; ++rr) {
+        const T xv = xs[rr][ta];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          acc[q] += (double)part[q];
-          part[q] = T(0);
+        for (int q = 0; q < 4; ++q) part[q] += xv * ys[rr][tb + 8 * q];
+        if ((rr & 15) == 15) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[q] += (double)part[q];
+            part[q] = T(0);
+          }
         }
       }
     }
@@ -78,13 +88,16 @@ __global__ void k_gram_rows(const T* __restrict__ A, int64_t lda, int m, int64_t
 // semidefinite G the column norms ||W_j|| = lambda_j. With JT = float the eigenvalues are
 // recomputed in FP64 as v_j^T G v_j / v_j^T v_j. Outputs: evals (n, descending), evecs (n x n
 // row-major, column j = eigenvector of evals[j]), sweeps in *info.
+// With vk_global set, the accumulated rotations live there (n x n, global memory) instead of in
+// shared memory, so that FP64 fits for every n <= 129.
 template <typename JT>
 __global__ void k_sym_eig(const double* __restrict__ G, int n, double* __restrict__ evals,
-                          double* __restrict__ evecs, int* info) {
+                          double* __restrict__ evecs, int* info, JT* vk_global) {
   extern __shared__ __align__(16) unsigned char smem[];
   JT* W = reinterpret_cast<JT*>(smem);
-  JT* VK = W + (size_t)n * n;
-  double* ev = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(VK + (size_t)n * n) + 15) & ~uintptr_t(15));
+  JT* VK = vk_global ? vk_global : W + (size_t)n * n;
+  JT* tail = vk_global ? W + (size_t)n * n : VK + (size_t)n * n;
+  double* ev = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
   int* perm = reinterpret_cast<int*>(ev + n);
   int* flag = perm + n;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -389,6 +402,78 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
   return x ^ (x >> 31);
+}
+
+// sq[j] += sum over a slice of rows of B[row, j]^2 in FP64 (j < r; sq zeroed by the caller).
+// Block (32 columns x 8 row lanes), grid (ceil(r / 32), row slices).
+template <typename T>
+__global__ void __launch_bounds__(256) k_col_sumsq(const T* __restrict__ B, int64_t rows, int64_t ldb, int r,
+                                                   int64_t rows_per_split, double* __restrict__ sq) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r1 = r0 + rows_per_split < rows ? r0 + rows_per_split : rows;
+  double acc = 0.0;
+  if (j < r)
+    for (int64_t row = r0 + warp; row < r1; row += 8) {
+      const double v = (double)B[row * ldb + j];
+      acc = fma(v, v, acc);
+    }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && j < r) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    atomicAdd(&sq[j], t);
+  }
+}
+
+// Singular values from column norms, descending: sig[jj] = sqrt(sq[perm[jj]]), inv[jj] = 1 / sig[jj]
+// (0 for a zero column); ties keep the column order. One block.
+__global__ void k_sort_norms(const double* __restrict__ sq, int r, double* __restrict__ sig, int* __restrict__ perm,
+                             double* __restrict__ inv) {
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    const double v = sq[j];
+    int rank = 0;
+    for (int l = 0; l < r; ++l) rank += (sq[l] > v) || (sq[l] == v && l < j);
+    const double sv = sqrt(fmax(v, 0.0));
+    perm[rank] = j;
+    sig[rank] = sv;
+    inv[rank] = sv > 0.0 ? 1.0 / sv : 0.0;
+  }
+}
+
+// out[row, jj] = in[row, perm[jj]] * scale[jj] (scale optional) for jj < r <= kKmaxLimit + 1; one
+// warp per row, staged through shared memory, so in and out may be the same array.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_permute_cols(const Tin* in, int64_t ldi, Tout* out, int64_t ldo, int64_t rows,
+                                                      int r, const int* __restrict__ perm,
+                                                      const double* __restrict__ scale) {
+  __shared__ double buf[8][kKmaxLimit + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+  if (row >= rows) return;
+  for (int c = lane; c < r; c += 32) buf[warp][c] = (double)in[row * ldi + c];
+  __syncwarp();
+  for (int jj = lane; jj < r; jj += 32) out[row * ldo + jj] = (Tout)(buf[warp][perm[jj]] * (scale ? scale[jj] : 1.0));
+}
+
+// Columns j < r of Q (rows x r, row stride ldq) whose singular value is at most rel * sig[0]
+// (or zero) are overwritten with SplitMix64 uniforms in [-1, 1): there A v_j / sigma_j is
+// dominated by rounding, so an orthonormal completion (the re-orthonormalisation that follows)
+// replaces it.
+template <typename T>
+__global__ void k_seed_small_cols(T* __restrict__ Q, int64_t rows, int64_t ldq, const double* __restrict__ sig, int r,
+                                  double rel, uint64_t seed) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * r) return;
+  const int64_t row = idx / r;
+  const int j = (int)(idx - row * r);
+  const double s0 = sig[0];
+  if (!(sig[j] <= rel * s0) && sig[j] > 0.0) return;
+  const uint64_t h = splitmix64(seed ^ (uint64_t)idx);
+  Q[row * ldq + j] = (T)((double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0);
 }
 
 // Test matrix Omega (rows x l, row stride ld): columns [0, c0) copied from W (warm start with the

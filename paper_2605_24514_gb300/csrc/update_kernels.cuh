@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
   in.delta = delta;
   __shared__ int s_sweeps;
   int k_out = -1;
-  if (sizeof(JT) < sizeof(double)) {
+  if (sizeof(JT) < sizeof(double) && KB <= kFastCoreMaxKB) {
     // Secular-equation core (O(k^2) roots + verification); -1 means "use the Jacobi path".
     int it = 0;
     k_out = core_fast_cta<T, KB>(in, core_smem, UK, VKo, ldo, sig, &it);

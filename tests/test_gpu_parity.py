@@ -293,3 +293,60 @@ def test_randomized_metrics_on_factor_panel(isvd, prec):
     assert abs(gm["frob_opt"] - om.frob_opt) <= 1e-2 * om.frob_opt
     assert abs(gm["frob_error"] - om.frob_error) <= 1e-4 * om.frob_error
     assert abs(gm["frob_ratio"] - om.frob_ratio) <= 1e-2 * om.frob_ratio
+
+
+def _spectrum_model(M, N, rank, seed):
+    """A M x N matrix of exact rank ``rank`` with singular values 10 * 0.96^i (relative gaps of
+    4%, so truncation picks the same directions on both sides), plus noise of 1e-7."""
+    g = rng(seed)
+    L, _ = np.linalg.qr(g.standard_normal((M, rank)))
+    R, _ = np.linalg.qr(g.standard_normal((N, rank)))
+    s = 10.0 * 0.96 ** np.arange(rank)
+    return (L * s) @ R.T + 1e-7 * g.standard_normal((M, N))
+
+
+@pytest.mark.parametrize("prec,k,k_max", [(1, 100, 128), (0, 90, 96)])
+def test_largest_rank_buckets(isvd, prec, k, k_max):
+    """Ranks above 64: the 128 bucket (FP32) and the FP64 ceiling of 96, with rows, columns and
+    entries cut from one fixed matrix so that the stream stays consistent."""
+    Af = _spectrum_model(260, 200, 120, seed=11)
+    m, n = 150, 130
+    A0 = Af[:m, :n].copy()
+    g, o = run_pair(isvd, A0, None, k, prec, k_max=k_max, row_cap=260, col_cap=200)
+    ev_rng = rng(12)
+    for e in range(40):
+        u = ev_rng.random()
+        if u < 0.5:
+            v = Af[m, :n]
+            v = v.astype(np.float32) if prec == 1 else v
+            g.append_row(v)
+            o.append_row(v.astype(np.float64))
+            m += 1
+        elif u < 0.75:
+            v = Af[:m, n]
+            v = v.astype(np.float32) if prec == 1 else v
+            g.append_col(v)
+            o.append_col(v.astype(np.float64))
+            n += 1
+        else:
+            i, j = int(ev_rng.integers(m)), int(ev_rng.integers(n))
+            d = float(ev_rng.normal(0, 0.005))
+            g.update_entry(i, j, d)
+            o.update_entry(i, j, d)
+        if e % 10 == 9:
+            compare(g, o, prec, f"k={k} event {e}")
+    assert g.shape()[:2] == (m, n)
+
+
+def test_handles_with_different_k_max_share_kernels(isvd):
+    """Handles whose k_max fall in one rank bucket (8 and 16) run the same kernel instantiation;
+    creating the smaller one after the larger must not break the larger one's launches."""
+    A0, fm = streams.make_panel(40, 30, 6, seed=21)
+    ev = streams.make_events(fm, 40, 30, mix=(0.6, 0.2, 0.2), seed=22)
+    ga, oa = run_pair(isvd, A0, ev, 12, 1, k_max=16)
+    gb, ob = run_pair(isvd, A0, ev, 4, 1, k_max=8)
+    for e in range(len(ev)):
+        feed(ga, oa, ev, e, 1)
+        feed(gb, ob, ev, e, 1)
+    compare(ga, oa, 1, "k_max 16")
+    compare(gb, ob, 1, "k_max 8")

@@ -90,7 +90,10 @@ def test_pool_matches_oracle_and_alone(isvd):
         A = pool.stream(ids[sidx]).matrix()
         np.testing.assert_allclose(A, o.A_view(), rtol=0, atol=1e-6)
         g.close()
-    assert pool.launches <= max(len(d[1]) for d in data) * 3
+    # per tick: per rank bucket a warp launch and a rotation launch (3 + 3), the hand-back
+    # launch, and one CTA launch per rank bucket with entry updates (3): independent of the
+    # number of streams
+    assert pool.launches <= max(len(d[1]) for d in data) * 10
     pool.close()
 
 
@@ -120,4 +123,155 @@ def test_pool_rejects_bad_ops_without_side_effects(isvd):
     assert e.value.name == "ESHAPE"
     U1, s1, V1 = pool.stream(sid).factors()
     assert np.array_equal(s0, s1)
+    pool.close()
+
+
+def _check_stream(pool, sid, o, tol=1e-5):
+    U, s, V = pool.stream(sid).factors()
+    Ro = o.reconstruction()
+    nrm = np.linalg.norm(Ro)
+    assert s.size == o.r
+    assert np.linalg.norm(recon(U, s, V) - Ro) <= tol * nrm
+    np.testing.assert_allclose(s, o.s, rtol=0, atol=tol * o.s[0])
+
+
+def test_pool_k64_bucket(isvd):
+    """k_max = 64 selects the widest fused-kernel bucket."""
+    data = make_streams(6, seed=11, n_events=10, ks=(40, 64), nrange=(90, 200))
+    pool = isvd.Pool(k_max=64)
+    factors = [oracle.truncated_svd(A0.astype(np.float64), k) for A0, _, k in data]
+    ids = [pool.admit(A0, k, factors=f) for (A0, _, k), f in zip(data, factors)]
+    ops, payload = interleave(ids, data)
+    pool.submit(ops, payload)
+    pool.sync()
+    for sidx, ((A0, ev, k), f) in enumerate(zip(data, factors)):
+        o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+        for e in range(len(ev)):
+            kd = int(ev.kind[e])
+            if kd == streams.ENTRY:
+                o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+            else:
+                o.apply(kd, ev.vector(e).astype(np.float32).astype(np.float64))
+        _check_stream(pool, ids[sidx], o)
+    pool.close()
+
+
+def _oracle_for(A0, ev, k, f, stop=None):
+    o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+    for e in range(len(ev) if stop is None else stop):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+        else:
+            o.apply(kd, ev.vector(e).astype(np.float32).astype(np.float64))
+    return o
+
+
+@pytest.mark.parametrize("k,k_max", [(6, 16), (40, 64)])
+def test_pool_long_side(isvd, k, k_max):
+    """Column appends on a 4,200-row panel. Rank capacity <= 32: the warp-per-update kernel (no
+    row buffer). Capacity 64: the CTA kernel's row buffer (4,096) is too short, so those appends
+    run through the single-stream kernels, in order, inside the same submit."""
+    A0, fm = streams.make_panel(4200, 48, 3, seed=13)
+    A0 = A0.astype(np.float32)
+    f = oracle.truncated_svd(A0.astype(np.float64), k)
+    pool = isvd.Pool(k_max=k_max)
+    sid = pool.admit(A0, k, factors=f)
+    ev = streams.make_events(fm, 4200, 8, mix=(0.3, 0.5, 0.2), seed=14)
+    ops, chunks, pos = [], [], 0
+    for e in range(len(ev)):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            ops.append((sid, kd, int(ev.i[e]), int(ev.j[e]), float(ev.delta[e]), 0, 0))
+        else:
+            v = ev.vector(e).astype(np.float32)
+            ops.append((sid, kd, 0, 0, 0.0, pos, v.size))
+            chunks.append(v)
+            pos += v.size
+    pool.submit(ops, np.concatenate(chunks))
+    pool.sync()
+    o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+    for e in range(len(ev)):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+        else:
+            o.apply(kd, ev.vector(e).astype(np.float32).astype(np.float64))
+    assert int(np.sum(ev.kind == streams.COL)) > 0
+    _check_stream(pool, sid, o)
+    pool.close()
+
+
+def _spectrum_panel(m, n, s, seed):
+    g = np.random.default_rng(seed)
+    L, _ = np.linalg.qr(g.standard_normal((m, len(s))))
+    R, _ = np.linalg.qr(g.standard_normal((n, len(s))))
+    return (L * np.asarray(s)) @ R.T, R
+
+
+def test_pool_warp_hand_back_paths(isvd):
+    """Updates the warp kernel hands to the CTA kernel (tied singular values, a zero row, an
+    empty factorisation) and ones it keeps (an in-span row, rank growth from a rank-deficient
+    start), all in one submit, each stream against the oracle."""
+    cases = []
+    # tied singular values: the core's poles coincide
+    A, R = _spectrum_panel(60, 30, [5.0, 3.0, 3.0, 3.0, 1.0, 0.5], seed=1)
+    g = np.random.default_rng(2)
+    rows = [R @ g.standard_normal(6) for _ in range(3)]
+    rows.insert(1, rows[0].copy())  # the same row twice: the next core has deflated weights
+    cases.append((A, 4, rows))
+    # zero row, then an in-span row (a combination of rows already in A)
+    A, R = _spectrum_panel(50, 20, [4.0, 2.0, 1.0], seed=3)
+    cases.append((A, 3, [np.zeros(20), 0.5 * A[3] - 2.0 * A[7], R @ np.array([1.0, -1.0, 0.5]) + 0.1]))
+    # rank-deficient start (exact rank 2, k = 8, both sides take their own initial SVD): the
+    # rank grows with each new direction
+    A, R = _spectrum_panel(40, 25, [3.0, 1.0], seed=4)
+    g = np.random.default_rng(5)
+    cases.append((A, 8, [g.standard_normal(25) for _ in range(5)]))
+    pool = isvd.Pool(k_max=16)
+    ids, fs = [], []
+    for ci, (A, k, _) in enumerate(cases):
+        f = oracle.truncated_svd(A, k) if ci < 2 else None
+        fs.append(f)
+        ids.append(pool.admit(A.astype(np.float32), k, factors=f))
+    ops, chunks, pos = [], [], 0
+    for t in range(max(len(c[2]) for c in cases)):
+        for sid, (_, _, rows) in zip(ids, cases):
+            if t < len(rows):
+                v = np.asarray(rows[t], np.float32)
+                ops.append((sid, streams.ROW, 0, 0, 0.0, pos, v.size))
+                chunks.append(v)
+                pos += v.size
+    pool.submit(ops, np.concatenate(chunks))
+    pool.sync()
+    for sid, (A, k, rows), f in zip(ids, cases, fs):
+        o = oracle.OracleISVD(A.astype(np.float32).astype(np.float64), k, tol_rel=3e-6, factors=f)
+        for v in rows:
+            o.append_row(np.asarray(v, np.float32).astype(np.float64))
+        _check_stream(pool, sid, o)
+        U, s, V = pool.stream(sid).factors()
+        assert np.abs(U.T.astype(np.float64) @ U - np.eye(s.size)).max() < 1e-4
+        assert np.abs(V.T.astype(np.float64) @ V - np.eye(s.size)).max() < 1e-4
+    pool.close()
+
+
+@pytest.mark.parametrize("k", [3, 8, 13, 16, 27, 32])
+def test_pool_warp_ranks_and_sides(isvd, k):
+    """Warp kernel at every row-load shape (rank not a multiple of 4, full buckets), rows and
+    columns interleaved, checked after every tick."""
+    A0, fm = streams.make_panel(90, 70, 40, seed=20 + k)
+    A0 = A0.astype(np.float32)
+    f = oracle.truncated_svd(A0.astype(np.float64), k)
+    ev = streams.make_events(fm, 90, 12, mix=(0.5, 0.5, 0.0), seed=40 + k)
+    pool = isvd.Pool(k_max=32)
+    sid = pool.admit(A0, k, factors=f)
+    o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+    for e in range(len(ev)):
+        v = ev.vector(e).astype(np.float32)
+        pool.submit([(sid, int(ev.kind[e]), 0, 0, 0.0, 0, v.size)], v)
+        o.apply(int(ev.kind[e]), v.astype(np.float64))
+        pool.sync()
+        _check_stream(pool, sid, o)
+    A = pool.stream(sid).matrix()
+    np.testing.assert_allclose(A, o.A_view(), rtol=0, atol=1e-6)
     pool.close()
