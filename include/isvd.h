@@ -284,6 +284,26 @@ int64_t isvd_pool_bytes_used(isvd_pool_t p);
 int64_t isvd_pool_kernel_launches(isvd_pool_t p);
 const char* isvd_pool_last_error(isvd_pool_t p);
 
+/* Launch classes of the pool's kernels, for isvd_pool_profile_read: the warp-per-update
+ * projection + core kernels and the row-parallel rotation kernels of rank buckets 8/16/32, the
+ * hand-back CTA kernel, and the CTA kernel (entry updates, rank bucket 64). */
+#define ISVD_POOL_KCLASS_WARP8 0
+#define ISVD_POOL_KCLASS_WARP16 1
+#define ISVD_POOL_KCLASS_WARP32 2
+#define ISVD_POOL_KCLASS_ROT8 3
+#define ISVD_POOL_KCLASS_ROT16 4
+#define ISVD_POOL_KCLASS_ROT32 5
+#define ISVD_POOL_KCLASS_RETRY 6
+#define ISVD_POOL_KCLASS_CTA 7
+#define ISVD_POOL_NUM_KCLASS 8
+
+/* enable != 0 clears and starts per-class timing of the pool's launches (CUDA events recorded on
+ * each launch's own stream); 0 stops it. Host cost: two event records per launch. */
+isvd_status isvd_pool_profile(isvd_pool_t p, int enable);
+/* Synchronizes the pool and writes, per launch class, the summed device time in ms (ms_out) and
+ * the number of launches (launches_out), each an array of n <= ISVD_POOL_NUM_KCLASS entries. */
+isvd_status isvd_pool_profile_read(isvd_pool_t p, double* ms_out, int64_t* launches_out, int n);
+
 /* --- allocation-free orthogonality measurement ----------------------------------------------
  * The paper has no counterpart: this is a library service for callers that cannot allocate
  * device memory, e.g. code running under a memory pool that forbids new allocations, code that

@@ -116,6 +116,8 @@ _SIGS = {
     "isvd_pool_bytes_used": (C.c_int64, [C.c_void_p]),
     "isvd_pool_kernel_launches": (C.c_int64, [C.c_void_p]),
     "isvd_pool_last_error": (C.c_char_p, [C.c_void_p]),
+    "isvd_pool_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "isvd_pool_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
 }
 
 
@@ -378,6 +380,21 @@ class Pool:
 
     def sync(self):
         self._check(lib().isvd_pool_sync(self._p), "isvd_pool_sync")
+
+    POOL_KCLASSES = ("warp8", "warp16", "warp32", "rot8", "rot16", "rot32", "retry", "cta")
+
+    def profile(self, enable=True):
+        """Per-launch-class device timing of subsequent submits (CUDA events on each launch's
+        own stream); enable=True clears and starts it."""
+        self._check(lib().isvd_pool_profile(self._p, 1 if enable else 0), "isvd_pool_profile")
+
+    def profile_read(self):
+        """{class: (ms, launches)} of the launches since profile(True)."""
+        n = len(self.POOL_KCLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        self._check(lib().isvd_pool_profile_read(self._p, ms, cnt, n), "isvd_pool_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.POOL_KCLASSES)}
 
     def stream(self, sid):
         h = lib().isvd_pool_stream(self._p, int(sid))

@@ -819,6 +819,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     key_hi[j] = kj.hi;
     key_lo[j] = kj.lo;
   }
+  for (int j = t; j < n; j += blockDim.x) perm[j] = j;  // a NaN key can misorder, never index out of range
   __syncthreads();
   for (int j = t; j < n; j += blockDim.x) {
     const float hj = key_hi[j], lj = key_lo[j];

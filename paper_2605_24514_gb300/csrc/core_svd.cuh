@@ -319,8 +319,10 @@ __device__ int core_svd_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VKo
       sref[j] = sig;
     }
   }
+  // Descending order, ties by index (stable); identity first, so a NaN value can misorder but
+  // never leave a slot unset.
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) perm[j] = j;
   __syncthreads();
-  // Descending order, ties by index (stable).
   for (int j = threadIdx.x; j < nc; j += blockDim.x) {
     const double sj = sref[j];
     int rank = 0;

@@ -1370,6 +1370,11 @@ struct isvd_pool_ctx {
   uint32_t gen = 0;
   std::vector<int32_t> touched;
   int64_t launches = 0, ticks = 0, fused_ops = 0, fallback_ops = 0, warp_ops = 0;
+  // Optional per-class launch timing (isvd_pool_profile).
+  int prof = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_used = 0;
+  std::vector<std::pair<int, size_t>> prof_spans;  // (class, index of the first of two events)
   std::string err;
 };
 
@@ -1380,9 +1385,33 @@ isvd_status pool_fail(isvd_pool_ctx* p, isvd_status s, const std::string& m) {
   return s;
 }
 
+// Profiling: an event pair around one launch on stream cs (nothing when profiling is off).
+cudaEvent_t pool_prof_event(isvd_pool_ctx* p) {
+  if (p->prof_used == p->prof_ev.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->prof_ev.push_back(e);
+  }
+  return p->prof_ev[p->prof_used++];
+}
+void pool_prof_begin(isvd_pool_ctx* p, cudaStream_t cs, int cls) {
+  if (!p->prof) return;
+  const size_t a = p->prof_used;
+  cudaEvent_t e0 = pool_prof_event(p), e1 = pool_prof_event(p);
+  if (!e0 || !e1) return;
+  cudaEventRecord(e0, cs);
+  p->prof_spans.push_back({cls, a});
+}
+void pool_prof_end(isvd_pool_ctx* p, cudaStream_t cs) {
+  if (!p->prof || p->prof_spans.empty()) return;
+  cudaEventRecord(p->prof_ev[p->prof_spans.back().second + 1], cs);
+}
+
 template <int KB>
 isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
+  pool_prof_begin(p, p->stream, ISVD_POOL_KCLASS_CTA);
   k_pool_tick<KB><<<count, pool_threads(KB), pool_smem_bytes<KB>(), p->stream>>>(ops);
+  pool_prof_end(p, p->stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool tick launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1396,8 +1425,10 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
                              const int* chunks, int* block_op) {
   const int blocks = (count + kWarpsPerBlock - 1) / kWarpsPerBlock;
   auto* scr = reinterpret_cast<RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
+  pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
   k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), cs>>>(ops, count, base, p->retry_list,
                                                                              p->retry_n + t, scr, chunks, block_op);
+  pool_prof_end(p, cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1409,7 +1440,9 @@ template <int KB>
 isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int base, const int* chunks,
                                const int* block_op, int nblocks) {
   auto* scr = reinterpret_cast<const RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
-  k_pool_rotate<KB><<<nblocks, kPoolRotRows, 0, cs>>>(ops, scr, chunks, block_op);
+  pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
+  k_pool_rotate<KB><<<nblocks, kPoolRotThreads, rot_smem_bytes<KB>(), cs>>>(ops, scr, chunks, block_op);
+  pool_prof_end(p, cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1419,7 +1452,9 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
 // The CTA kernel over the updates the warps of tick t handed back (ops = the tick's warp ops).
 isvd_status pool_launch_retry(isvd_pool_ctx* p, const PoolOp* ops, int count, int t) {
   const int rblocks = std::min(count, p->num_sms);
+  pool_prof_begin(p, p->stream, ISVD_POOL_KCLASS_RETRY);
   k_pool_retry<32><<<rblocks, pool_threads(32), pool_smem_bytes<32>(), p->stream>>>(ops, p->retry_list, p->retry_n + t);
+  pool_prof_end(p, p->stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool retry launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1464,6 +1499,12 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_pool_retry<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>());
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_rotate<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_rotate<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pool_rotate<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<8>());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_pool_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<8>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_pool_warp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<16>());
@@ -1504,6 +1545,7 @@ void isvd_pool_destroy(isvd_pool_t p) {
     if (p->ev_r[i]) cudaEventDestroy(p->ev_r[i]);
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->chunks_dev) cudaFree(p->chunks_dev);
   if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
   if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
@@ -1520,10 +1562,13 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   for (isvd_ctx* h : p->streams) live += h != nullptr;
   if (live >= p->max_streams) return pool_fail(p, ISVD_EBUDGET, "pool: stream slots exhausted");
   isvd_config c = p->cfg;
-  c.k_max = k;  // the stream's rank capacity selects its fused-kernel bucket
+  // The stream's rank capacity is its fused-kernel bucket (8, 16, 32 or 64): U and V rows are then
+  // exactly one bucket wide, which the batched kernels read as contiguous float4 arrays. The
+  // working rank stays k.
+  c.k_max = pool_bucket(k);
   c.row_cap = std::max<int64_t>(row_cap, m0 + 1);
   c.col_cap = std::max<int64_t>(col_cap, n0 + 1);
-  const int64_t need = stream_footprint(c.row_cap, c.col_cap, round_up(k, 4));
+  const int64_t need = stream_footprint(c.row_cap, c.col_cap, c.k_max);
   if (p->budget > 0 && p->used + need > p->budget)
     return pool_fail(p, ISVD_EBUDGET, "pool: HBM budget exceeded (" + std::to_string(p->used + need) + " > " +
                                           std::to_string(p->budget) + " bytes)");
@@ -1578,6 +1623,36 @@ isvd_t isvd_pool_stream(isvd_pool_t p, int32_t sid) {
 int64_t isvd_pool_bytes_used(isvd_pool_t p) { return p ? p->used : 0; }
 
 int64_t isvd_pool_kernel_launches(isvd_pool_t p) { return p ? p->launches : 0; }
+
+isvd_status isvd_pool_profile(isvd_pool_t p, int enable) {
+  if (!p) return ISVD_EINVAL;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool profile");
+  p->prof = enable ? 1 : 0;
+  if (enable) {
+    p->prof_used = 0;
+    p->prof_spans.clear();
+  }
+  return ISVD_OK;
+}
+
+isvd_status isvd_pool_profile_read(isvd_pool_t p, double* ms_out, int64_t* launches_out, int n) {
+  if (!p || !ms_out || !launches_out || n < 0 || n > ISVD_POOL_NUM_KCLASS) return ISVD_EINVAL;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool profile read");
+  for (int c = 0; c < n; ++c) {
+    ms_out[c] = 0.0;
+    launches_out[c] = 0;
+  }
+  for (const auto& sp : p->prof_spans) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->prof_ev[sp.second], p->prof_ev[sp.second + 1]) != cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool profile read");
+    if (sp.first < n) {
+      ms_out[sp.first] += ms;
+      launches_out[sp.first] += 1;
+    }
+  }
+  return ISVD_OK;
+}
 
 isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, const void* payload,
                              int64_t payload_len, int payload_on_device) {

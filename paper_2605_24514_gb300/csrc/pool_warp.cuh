@@ -157,6 +157,60 @@ __device__ __forceinline__ void warp_rotate_row(float* y, const float (&xv)[KB],
   }
 }
 
+// Two rows at once (y1 only when has1): every U_K / V_K value read from shared memory feeds both
+// rows, which halves the shared-memory traffic per FMA (the rotation kernel's bound otherwise).
+template <int KB>
+__device__ __forceinline__ void rotate_two_rows(float* y0, float* y1, const float (&x0)[KB], const float (&x1)[KB],
+                                                int r, const float* R, int k_out, float z0, float z1, bool withz,
+                                                bool has1) {
+#pragma unroll 1
+  for (int h0 = 0; h0 < k_out; h0 += 8) {
+    float o0[8], o1[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) o0[jj] = o1[jj] = 0.f;
+#pragma unroll
+    for (int c = 0; c <= KB; ++c) {
+      if (c < r || (c == r && withz)) {
+        const float4* rr = reinterpret_cast<const float4*>(R + c * KB + h0);
+        const float4 a = rr[0], b = rr[1];
+        const float u0 = c < r ? x0[c < KB ? c : 0] : z0;
+        const float u1 = c < r ? x1[c < KB ? c : 0] : z1;
+        o0[0] = fmaf(u0, a.x, o0[0]);
+        o0[1] = fmaf(u0, a.y, o0[1]);
+        o0[2] = fmaf(u0, a.z, o0[2]);
+        o0[3] = fmaf(u0, a.w, o0[3]);
+        o0[4] = fmaf(u0, b.x, o0[4]);
+        o0[5] = fmaf(u0, b.y, o0[5]);
+        o0[6] = fmaf(u0, b.z, o0[6]);
+        o0[7] = fmaf(u0, b.w, o0[7]);
+        o1[0] = fmaf(u1, a.x, o1[0]);
+        o1[1] = fmaf(u1, a.y, o1[1]);
+        o1[2] = fmaf(u1, a.z, o1[2]);
+        o1[3] = fmaf(u1, a.w, o1[3]);
+        o1[4] = fmaf(u1, b.x, o1[4]);
+        o1[5] = fmaf(u1, b.y, o1[5]);
+        o1[6] = fmaf(u1, b.z, o1[6]);
+        o1[7] = fmaf(u1, b.w, o1[7]);
+      }
+    }
+    if (h0 + 7 < k_out) {
+      *reinterpret_cast<float4*>(y0 + h0) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+      *reinterpret_cast<float4*>(y0 + h0 + 4) = make_float4(o0[4], o0[5], o0[6], o0[7]);
+      if (has1) {
+        *reinterpret_cast<float4*>(y1 + h0) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+        *reinterpret_cast<float4*>(y1 + h0 + 4) = make_float4(o1[4], o1[5], o1[6], o1[7]);
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (h0 + jj < k_out) {
+          y0[h0 + jj] = o0[jj];
+          if (has1) y1[h0 + jj] = o1[jj];
+        }
+    }
+  }
+}
+
 // Next non-deflated pole above j (bit set in mask), or -1.
 __device__ __forceinline__ int warp_next_pole(uint64_t mask, int j) {
   const uint64_t m = j + 1 < 64 ? (mask >> (j + 1)) : 0ull;
@@ -179,51 +233,105 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   const int64_t nQ = is_row ? op.m : op.n;
   const int64_t ld = op.ld;
   const float* x = op.x;
-  if (r < 1 || r > KB) return false;
+  if (r < 1 || r > KB || ld != KB) return false;
   ISVD_WSTAMP_INIT(tp);
 
+  // The projection side as one contiguous float4 array (row stride ld == KB): lane L reads chunk
+  // (L mod CPL) of row (L div CPL) + RPW i, so every load is coalesced and four are in flight;
+  // columns >= r are masked (stale values beyond the working rank).
+  constexpr int CPL = KB / 4;    // float4 chunks per row
+  constexpr int RPW = 32 / CPL;  // rows per warp-wide load
+  constexpr int U4 = 4;          // loads in flight per lane
+  const int cq = lane % CPL;
+  const float4* P4 = reinterpret_cast<const float4*>(P);
+  const int64_t nF = nP * CPL;
+  float msk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) msk[j] = 4 * cq + j < r ? 1.f : 0.f;
+
   // Pass 1: p1 = P^T x and ||x||^2.
-  float acc[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
+  float a4[4] = {0.f, 0.f, 0.f, 0.f};
   ff xx{0.f, 0.f};
-  for (int64_t row = lane; row < nP; row += 32) {
-    float pv[KB];
-    warp_load_row<KB>(P + row * ld, r, pv);
-    const float xv = x[row];
+  for (int64_t fb = 0; fb < nF; fb += 32 * U4) {  // warp-uniform trip count
+    float4 v[U4];
+    float xv[U4];
 #pragma unroll
-    for (int c = 0; c < KB; ++c) acc[c] = fmaf(pv[c], xv, acc[c]);
-    xx = ff_add(xx, two_prod(xv, xv));
+    for (int u = 0; u < U4; ++u) {
+      const int64_t f = fb + lane + 32 * u;
+      const bool ok = f < nF;
+      v[u] = ok ? P4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[u] = ok ? x[f / CPL] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U4; ++u) {
+      a4[0] = fmaf(v[u].x * msk[0], xv[u], a4[0]);
+      a4[1] = fmaf(v[u].y * msk[1], xv[u], a4[1]);
+      a4[2] = fmaf(v[u].z * msk[2], xv[u], a4[2]);
+      a4[3] = fmaf(v[u].w * msk[3], xv[u], a4[3]);
+      if (cq == 0) xx = ff_add(xx, two_prod(xv[u], xv[u]));
+    }
   }
-  const float p1c = warp_transpose_sum<KB>(acc, lane);  // p1[lane % KB]
+#pragma unroll
+  for (int o = CPL; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a4[j] += __shfl_xor_sync(kFull, a4[j], o);
   xx = ff_group_sum<32>(xx);
-  if (lane < KB) S.ph[lane] = lane < r ? p1c : 0.f;
+  if (lane < CPL)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S.ph[4 * lane + j] = msk[j] * a4[j];
   __syncwarp();
   ISVD_WSTAMP(17, tp);
 
-  // Pass 2 (CGS2): z1 = x - P p1 per row in float-float, p2 = P^T z1, ||z1||^2.
+  // Pass 2 (CGS2): z1 = x - P p1 per row (float-float, the row's CPL lanes combine their chunks),
+  // p2 = P^T z1, ||z1||^2.
+  float p1c[4];
 #pragma unroll
-  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
+  for (int j = 0; j < 4; ++j) p1c[j] = S.ph[4 * cq + j];
+  float b4[4] = {0.f, 0.f, 0.f, 0.f};
   ff zz{0.f, 0.f};
-  for (int64_t row = lane; row < nP; row += 32) {
-    float pv[KB];
-    warp_load_row<KB>(P + row * ld, r, pv);
-    ff s{x[row], 0.f};
+  for (int64_t fb = 0; fb < nF; fb += 32 * U4) {  // warp-uniform trip count
+    float4 v[U4];
+    float xv[U4];
 #pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      if (c < r) {
-        const ff pr = two_prod(pv[c], S.ph[c]);
-        s = ff_add(s, ff{-pr.hi, -pr.lo});
-      }
+    for (int u = 0; u < U4; ++u) {
+      const int64_t f = fb + lane + 32 * u;
+      const bool ok = f < nF;
+      v[u] = ok ? P4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[u] = ok ? x[f / CPL] : 0.f;
     }
-    const float z1 = s.hi + s.lo;
 #pragma unroll
-    for (int c = 0; c < KB; ++c) acc[c] = fmaf(pv[c], z1, acc[c]);
-    zz = ff_add(zz, ff_sqr(s));
+    for (int u = 0; u < U4; ++u) {
+      const float vv[4] = {v[u].x * msk[0], v[u].y * msk[1], v[u].z * msk[2], v[u].w * msk[3]};
+      ff d = two_prod(vv[0], p1c[0]);
+#pragma unroll
+      for (int j = 1; j < 4; ++j) d = ff_add(d, two_prod(vv[j], p1c[j]));
+      d = ff_group_sum<CPL>(d);
+      const ff zrow = ff_add(ff{xv[u], 0.f}, ff{-d.hi, -d.lo});
+      const float z1 = zrow.hi + zrow.lo;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b4[j] = fmaf(vv[j], z1, b4[j]);
+      if (cq == 0) zz = ff_add(zz, ff_sqr(zrow));
+    }
   }
-  const float p2c = warp_transpose_sum<KB>(acc, lane);  // p2[lane % KB]
+#pragma unroll
+  for (int o = CPL; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b4[j] += __shfl_xor_sync(kFull, b4[j], o);
   zz = ff_group_sum<32>(zz);
-  double pn = (lane < KB && lane < r) ? (double)p2c * (double)p2c : 0.0;
+  // p1 and p2 for column c = 4 lane + j on lanes < CPL; spread to one column per lane.
+  float p1v = 0.f, p2v = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float t1 = __shfl_sync(kFull, a4[j], (lane >> 2) % CPL);
+    const float t2 = __shfl_sync(kFull, b4[j], (lane >> 2) % CPL);
+    if ((lane & 3) == j) {
+      p1v = t1;
+      p2v = t2;
+    }
+  }
+  const float p1c_l = (lane < KB && lane < r) ? p1v : 0.f;  // p1[lane]
+  const float p2c = (lane < KB && lane < r) ? p2v : 0.f;    // p2[lane]
+  double pn = (double)p2c * (double)p2c;
   pn = warp_sum(pn);
   const double xn2 = (double)xx.hi + (double)xx.lo;
   const double rho2 = ((double)zz.hi + (double)zz.lo) - pn;
@@ -238,7 +346,7 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   __syncwarp();
   if (lane < KB) {
     float hi, lo;
-    two_sum(p1c, p2c, hi, lo);
+    two_sum(p1c_l, p2c, hi, lo);
     S.ph[lane] = lane < r ? hi : 0.f;
     S.pl[lane] = lane < r ? lo : 0.f;
   }
@@ -400,7 +508,10 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     return false;
   }
 
-  // Descending order of the roots (compared as float pairs, ties by index).
+  // Descending order of the roots (compared as float pairs, ties by index). Every slot must be
+  // filled exactly once; anything else (a NaN root) hands the update back.
+  for (int j = lane; j < nc; j += 32) S.perm[j] = -1;
+  __syncwarp();
   for (int j = lane; j < nc; j += 32) {
     const float hj = S.lhi[j], lj = S.llo[j];
     int rk = 0;
@@ -408,9 +519,12 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
       const float hl = S.lhi[l], ll = S.llo[l];
       rk += (hl > hj) || (hl == hj && (ll > lj || (ll == lj && l < j)));
     }
-    S.perm[rk] = j;
+    if (rk < nc) S.perm[rk] = j;
   }
   __syncwarp();
+  int unset = 0;
+  for (int j = lane; j < nc; j += 32) unset |= S.perm[j] < 0;
+  if (__any_sync(kFull, unset)) return false;
   const int k_out = kt < nc ? kt : nc;
   ISVD_WSTAMP(21, tp);
 
@@ -490,9 +604,10 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
 // ops[0 .. count): row/column appends of streams in rank bucket KB, one warp each. Updates that
 // need the CTA kernel are listed in retry[] as base + index (count in *retry_n), untouched.
 // Also fills block_op[chunk_start[e] + i] = e for the update's rotation blocks.
-constexpr int kPoolRotRows = 128;
+constexpr int kPoolRotThreads = 128;
+constexpr int kPoolRotRows = 2 * kPoolRotThreads;  // rows per rotation block (two per thread)
 template <int KB>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 8 ? 8 : KB <= 16 ? 6 : 5)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
     k_pool_warp(const PoolOp* __restrict__ ops, int count, int base, int* __restrict__ retry,
                 int* __restrict__ retry_n, RotScratch<KB>* __restrict__ scratch, const int* __restrict__ chunk_start,
                 int* __restrict__ block_op) {
@@ -515,17 +630,28 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 8 ? 8 : KB <= 16 ? 
   }
 }
 
-// Rotations of the warp kernel's updates: block b rotates 128 rows of one side of update
-// e = block_op[b] (chunk_start[e] = its first block; per update ceil(nP / 128) blocks for the
-// projection side, then ceil(nQ / 128) for the other), one thread per row, V_K or U_K in shared
-// memory.
+// Rotations of the warp kernel's updates: block b rotates kPoolRotRows rows of one side of update
+// e = block_op[b] (chunk_start[e] = its first block; per update ceil(nP / kPoolRotRows) blocks for
+// the projection side, then ceil(nQ / kPoolRotRows) for the other). Rows are KB floats wide and
+// contiguous, so the block's rows form one contiguous tile: it is read and written with coalesced
+// float4 accesses through a padded shared-memory copy (row stride KB + 4 floats, conflict-free
+// for a thread reading its own row), and each thread rotates two rows from there.
+constexpr int kRotPad = 4;
 template <int KB>
-__global__ void __launch_bounds__(kPoolRotRows) k_pool_rotate(const PoolOp* __restrict__ ops,
-                                                              const RotScratch<KB>* __restrict__ scratch,
-                                                              const int* __restrict__ chunk_start,
-                                                              const int* __restrict__ block_op) {
-  __shared__ __align__(16) float R[(KB + 1) * KB];
-  __shared__ float ph[KB], pl[KB];
+constexpr size_t rot_smem_bytes() {
+  return ((size_t)kPoolRotRows * (KB + kRotPad) + (size_t)(KB + 1) * KB + 2 * KB) * sizeof(float);
+}
+template <int KB>
+__global__ void __launch_bounds__(kPoolRotThreads, KB <= 16 ? 6 : 4)
+    k_pool_rotate(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
+                  const int* __restrict__ chunk_start, const int* __restrict__ block_op) {
+  extern __shared__ __align__(16) float rsm[];
+  constexpr int LS = KB + kRotPad;  // padded row stride of the tile
+  constexpr int C4 = KB / 4;        // float4 chunks per row
+  float* T = rsm;                   // kPoolRotRows x LS
+  float* R = T + kPoolRotRows * LS;  // (KB + 1) x KB
+  float* ph = R + (KB + 1) * KB;
+  float* pl = ph + KB;
   const int b = blockIdx.x;
   const int e = block_op[b];
   const RotScratch<KB>& sc = scratch[e];
@@ -540,34 +666,56 @@ __global__ void __launch_bounds__(kPoolRotRows) k_pool_rotate(const PoolOp* __re
   const bool pside = ci < cP;
   const int r = sc.r;
   const bool withz = pside && sc.grew;
+  const int64_t nrows = pside ? nP : nQ;
+  const int64_t base = (int64_t)(pside ? ci : ci - cP) * kPoolRotRows;
+  const int rows = (int)(nrows - base < kPoolRotRows ? nrows - base : kPoolRotRows);
+  float* X = pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V);
+  float4* X4 = reinterpret_cast<float4*>(X + base * KB);
   const float* src = pside ? sc.RP : sc.RQ;
-  for (int idx = threadIdx.x; idx < (r + 1) * KB; idx += kPoolRotRows) R[idx] = src[idx];
+  for (int idx = threadIdx.x; idx < (r + 1) * KB; idx += kPoolRotThreads) R[idx] = src[idx];
   if (withz)
-    for (int c = threadIdx.x; c < r; c += kPoolRotRows) {
+    for (int c = threadIdx.x; c < r; c += kPoolRotThreads) {
       ph[c] = sc.ph[c];
       pl[c] = sc.pl[c];
     }
-  __syncthreads();
-  const int64_t row = (int64_t)(pside ? ci : ci - cP) * kPoolRotRows + threadIdx.x;
-  if (row >= (pside ? nP : nQ)) return;
-  float* X = pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V);
-  float* xr = X + row * (int64_t)op.ld;
-  float xv[KB];
-  warp_load_row<KB>(xr, r, xv);
-  float zh = 0.f;
-  if (withz) {
-    ff s{op.x[row], 0.f};
-#pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      if (c < r) {
-        ff q = two_prod(xv[c], ph[c]);
-        q.lo = fmaf(xv[c], pl[c], q.lo);
-        s = ff_add(s, ff{-q.hi, -q.lo});
-      }
-    }
-    zh = (s.hi + s.lo) * sc.inv_rho;
+  for (int f = threadIdx.x; f < rows * C4; f += kPoolRotThreads) {
+    const int rr = f / C4, q = f - rr * C4;
+    *reinterpret_cast<float4*>(T + rr * LS + 4 * q) = X4[f];
   }
-  warp_rotate_row<KB>(xr, xv, r, R, k_out, zh, withz);
+  __syncthreads();
+  const int t0 = threadIdx.x, t1 = threadIdx.x + kPoolRotThreads;
+  if (t0 < rows) {
+    const bool has1 = t1 < rows;
+    float* y0 = T + t0 * LS;
+    float* y1 = T + (has1 ? t1 : t0) * LS;
+    float x0[KB], x1[KB];
+    warp_load_row<KB>(y0, r, x0);
+    warp_load_row<KB>(y1, r, x1);
+    float z0 = 0.f, z1 = 0.f;
+    if (withz) {
+      ff s0{op.x[base + t0], 0.f}, s1{op.x[base + (has1 ? t1 : t0)], 0.f};
+#pragma unroll
+      for (int c = 0; c < KB; ++c) {
+        if (c < r) {
+          ff q = two_prod(x0[c], ph[c]);
+          q.lo = fmaf(x0[c], pl[c], q.lo);
+          s0 = ff_add(s0, ff{-q.hi, -q.lo});
+          q = two_prod(x1[c], ph[c]);
+          q.lo = fmaf(x1[c], pl[c], q.lo);
+          s1 = ff_add(s1, ff{-q.hi, -q.lo});
+        }
+      }
+      z0 = (s0.hi + s0.lo) * sc.inv_rho;
+      z1 = (s1.hi + s1.lo) * sc.inv_rho;
+    }
+    rotate_two_rows<KB>(y0, y1, x0, x1, r, R, k_out, z0, z1, withz, has1);
+  }
+  __syncthreads();
+  // Columns >= k_out keep whatever the tile held (stale, never read: the working rank is k_out).
+  for (int f = threadIdx.x; f < rows * C4; f += kPoolRotThreads) {
+    const int rr = f / C4, q = f - rr * C4;
+    X4[f] = *reinterpret_cast<const float4*>(T + rr * LS + 4 * q);
+  }
 }
 
 }  // namespace isvd

@@ -133,6 +133,7 @@ __global__ void k_sym_eig(const double* __restrict__ G, int n, double* __restric
     }
     if (lane == 0) ev[j] = lam;
   }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) perm[j] = j;  // NaN-safe: no slot left unset
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const double sj = ev[j];
@@ -433,6 +434,12 @@ __global__ void __launch_bounds__(256) k_col_sumsq(const T* __restrict__ B, int6
 // (0 for a zero column); ties keep the column order. One block.
 __global__ void k_sort_norms(const double* __restrict__ sq, int r, double* __restrict__ sig, int* __restrict__ perm,
                              double* __restrict__ inv) {
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {  // NaN-safe defaults: no slot left unset
+    perm[j] = j;
+    sig[j] = 0.0;
+    inv[j] = 0.0;
+  }
+  __syncthreads();
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     const double v = sq[j];
     int rank = 0;
