@@ -41,8 +41,8 @@ WORKLOADS = {
                                      "FP32 bulk + FP64 core/rho/sigma, refresh on ratio>1.05 or angle>5deg"),
     "batched-4096": dict(prec="fp32", batch=4096, streams=4096, n_lo=50, n_hi=500, ks=(8, 16, 32),
                          desc="4096 independent factor-model streams, n ~ U[50,500], m0 = 2n, k ~ {8,16,32}, "
-                              "one row append per stream per tick, FP32 bulk + FP64-class core; fused per-tick "
-                              "launch vs per-stream single-stream kernels (plain GPU form)"),
+                              "one row append per stream per tick, FP32 bulk + FP64-class core; batched pool path "
+                              "vs per-stream single-stream kernels (plain GPU form)"),
     "panel-200x50-k10": dict(prec="fp64", check_every=50, T_refresh=250, batch=200,
                              desc="200x50 factor panel (5 factors), k=10, 1000 row appends then 200 entry "
                                   "updates, FP64, periodic refresh 250, metrics every 50"),

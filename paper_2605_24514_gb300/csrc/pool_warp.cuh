@@ -237,10 +237,9 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   ISVD_WSTAMP_INIT(tp);
 
   // The projection side as one contiguous float4 array (row stride ld == KB): lane L reads chunk
-  // (L mod CPL) of row (L div CPL) + RPW i, so every load is coalesced and four are in flight;
+  // (L mod CPL) of row (L div CPL) + (32 / CPL) i, so every load is coalesced and four are in flight;
   // columns >= r are masked (stale values beyond the working rank).
   constexpr int CPL = KB / 4;    // float4 chunks per row
-  constexpr int RPW = 32 / CPL;  // rows per warp-wide load
   constexpr int U4 = 4;          // loads in flight per lane
   const int cq = lane % CPL;
   const float4* P4 = reinterpret_cast<const float4*>(P);
