@@ -282,7 +282,7 @@ __device__ bool secular_cta(int n, const float* dhi, const float* dlo, const flo
 // checked against tol_bw ||w|| (a failed check, like a deflated rho pole, returns false).
 // V: n x n, column j at V + j n, rows in original order (row[]); U: nr x n with column stride nr
 // (row i < r is sigma_i's, row r the new row's); sf = float sigma in original order.
-__device__ bool ge_append_vectors(int n, int r, int nr, const float* dhi, const float* dlo, const float* w,
+static __device__ bool ge_append_vectors(int n, int r, int nr, const float* dhi, const float* dlo, const float* w,
                                   const int* row, const int* nxt, const float* tau, const int* org, const float* sf,
                                   float* what, float* V, float* U, float wn2, float tol_bw, int* s_flag) {
   const int t = threadIdx.x;

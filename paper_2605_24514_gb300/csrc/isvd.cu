@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/isvd.h"
+#include "launch.cuh"
 #include "pool_kernels.cuh"
 #include "pool_warp.cuh"
 #include "refresh_kernels.cuh"
@@ -222,17 +223,8 @@ template <typename T>
 isvd_status launch_core(isvd_ctx* h, int kind, int64_t i, int64_t j, double delta) {
   const size_t cs = core_kernel_smem<T>(h->kmax);
   const int th = core_threads(h->kmax);
-  T* U = (T*)h->U;
-  T* V = (T*)h->V;
-  T* A = (T*)h->A;
-#define ISVD_CORE_ARGS kind, h->st, h->sig, h->p, U, V, h->ld, i, j, delta, A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld
-  switch (kb_bucket(h->kmax)) {
-    case 16: k_core<T, T, 16><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
-    case 32: k_core<T, T, 32><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
-    case 64: k_core<T, T, 64><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
-    default: k_core<T, T, 128><<<1, th, cs, h->stream>>>(ISVD_CORE_ARGS); break;
-  }
-#undef ISVD_CORE_ARGS
+  CK(h, core_launch<T>(kb_bucket(h->kmax), th, cs, h->stream, kind, h->st, h->sig, h->p, (T*)h->U, (T*)h->V, h->ld, i,
+                       j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld));
   CKL(h);
   return ISVD_OK;
 }
@@ -252,14 +244,9 @@ isvd_status set_attrs(isvd_ctx* h) {
   // The attribute is process-wide per template, so each bucket gets the shared memory of the
   // largest k_max it serves (handles with different k_max share one instantiation).
   const int kcap = sizeof(T) == sizeof(double) ? 96 : kKmaxLimit;
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_kernel_smem<T>(16)));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_kernel_smem<T>(32)));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_kernel_smem<T>(64)));
-  CK(h, cudaFuncSetAttribute(k_core<T, T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_kernel_smem<T>(kcap)));
+  const size_t core_smem[4] = {core_kernel_smem<T>(16), core_kernel_smem<T>(32), core_kernel_smem<T>(64),
+                                core_kernel_smem<T>(kcap)};
+  CK(h, core_set_attrs<T>(core_smem));
   CK(h, cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   CK(h, cudaFuncSetAttribute(k_chol_rinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1410,9 +1397,8 @@ void pool_prof_end(isvd_pool_ctx* p, cudaStream_t cs) {
 template <int KB>
 isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
   pool_prof_begin(p, p->stream, ISVD_POOL_KCLASS_CTA);
-  k_pool_tick<KB><<<count, pool_threads(KB), pool_smem_bytes<KB>(), p->stream>>>(ops);
+  cudaError_t e = pool_tick_launch<KB>(count, p->stream, ops);
   pool_prof_end(p, p->stream);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool tick launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
@@ -1423,13 +1409,10 @@ isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
 template <int KB>
 isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, int base, int t,
                              const int* chunks, int* block_op) {
-  const int blocks = (count + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  auto* scr = reinterpret_cast<RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
+  void* scr = static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
-  k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), cs>>>(ops, count, base, p->retry_list,
-                                                                             p->retry_n + t, scr, chunks, block_op);
+  cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op);
   pool_prof_end(p, cs);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
@@ -1439,11 +1422,10 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
 template <int KB>
 isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int base, const int* chunks,
                                const int* block_op, int nblocks) {
-  auto* scr = reinterpret_cast<const RotScratch<KB>*>(static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride);
+  const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
-  k_pool_rotate<KB><<<nblocks, kPoolRotThreads, rot_smem_bytes<KB>(), cs>>>(ops, scr, chunks, block_op);
+  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op);
   pool_prof_end(p, cs);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
@@ -1453,9 +1435,8 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
 isvd_status pool_launch_retry(isvd_pool_ctx* p, const PoolOp* ops, int count, int t) {
   const int rblocks = std::min(count, p->num_sms);
   pool_prof_begin(p, p->stream, ISVD_POOL_KCLASS_RETRY);
-  k_pool_retry<32><<<rblocks, pool_threads(32), pool_smem_bytes<32>(), p->stream>>>(ops, p->retry_list, p->retry_n + t);
+  cudaError_t e = pool_retry_launch(rblocks, p->stream, ops, p->retry_list, p->retry_n + t);
   pool_prof_end(p, p->stream);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool retry launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
@@ -1489,27 +1470,12 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->cfg.cuda_stream = cfg->cuda_stream;
   p->cfg.orth_every = (int64_t)1 << 62;  // the pool path runs no monitor; isvd_reorthogonalize on demand
   p->cfg.rsvd_power_iters = -1;
-  cudaError_t e = cudaFuncSetAttribute(k_pool_tick<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<8>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_tick<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<16>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_tick<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_tick<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<64>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_retry<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pool_smem_bytes<32>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_rotate<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<32>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_rotate<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<16>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_rotate<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem_bytes<8>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<8>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_warp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<16>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pool_warp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_block_smem<32>());
+  cudaError_t e = pool_tick_set_attr<8>();
+  if (e == cudaSuccess) e = pool_tick_set_attr<16>();
+  if (e == cudaSuccess) e = pool_tick_set_attr<32>();
+  if (e == cudaSuccess) e = pool_tick_set_attr<64>();
+  if (e == cudaSuccess) e = pool_retry_set_attr();
+  if (e == cudaSuccess) e = pool_warp_set_attrs();
   if (e == cudaSuccess) {
     int dev = 0;
     e = cudaGetDevice(&dev);

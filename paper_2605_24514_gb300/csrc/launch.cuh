@@ -1,0 +1,43 @@
+// Host-side launchers of the heavy kernel families, each compiled in a translation unit of its own
+// (core_f32.cu, core_f64.cu, pool_tick8/16/32/64.cu, pool_retry.cu, pool_warp.cu) so that the
+// library builds in parallel. The templates are defined in those units and explicitly instantiated
+// there. Every launcher enqueues one launch on stream s and returns cudaGetLastError(); the
+// set_attr(s) functions raise the dynamic shared-memory limit of the kernels they name.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "isvd_common.cuh"
+
+namespace isvd {
+
+struct PoolOp;
+
+// Core SVD kernel k_core<T, T, kb> (one CTA; kb = rank bucket 16/32/64/128).
+template <typename T>
+cudaError_t core_launch(int kb, int threads, size_t smem, cudaStream_t s, int kind, DevState* st, double* sig,
+                        const double* p, const T* U, const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A,
+                        int64_t lda, T* UK, T* VKo, int ldo);
+// smem[b] = dynamic shared memory of bucket 16 << b (b = 0..3).
+template <typename T>
+cudaError_t core_set_attrs(const size_t smem[4]);
+
+// Pool CTA kernels k_pool_tick<KB> (KB = 8/16/32/64, one translation unit each) and
+// k_pool_retry<32> (its own unit).
+template <int KB>
+cudaError_t pool_tick_launch(int count, cudaStream_t s, const PoolOp* ops);
+template <int KB>
+cudaError_t pool_tick_set_attr();
+cudaError_t pool_retry_launch(int blocks, cudaStream_t s, const PoolOp* ops, const int* retry, const int* retry_n);
+cudaError_t pool_retry_set_attr();
+
+// Pool warp-per-update kernels k_pool_warp<kb> and row-parallel rotations k_pool_rotate<kb>
+// (kb = 8/16/32); scratch is the bucket run's first RotScratch<kb> record.
+cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
+                             void* scratch, const int* chunks, int* block_op);
+cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
+                               const int* chunks, const int* block_op);
+cudaError_t pool_warp_set_attrs();
+
+}  // namespace isvd
