@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/isvd.h"
@@ -211,11 +212,32 @@ int core_threads(int kmax) {
   return warps * 32;
 }
 
+// True iff no element is Inf or NaN. Those are exactly the IEEE values whose exponent field is all
+// ones, so the scan tests that field branch-free over fixed-size blocks (a constant trip count the
+// host compiler vectorises at -O2) and stops after the first block holding a non-finite value.
 template <typename T>
 bool host_finite(const T* v, int64_t len) {
-  for (int64_t i = 0; i < len; ++i)
-    if (!std::isfinite((double)v[i])) return false;
-  return true;
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "float or double");
+  using B = typename std::conditional<sizeof(T) == 4, uint32_t, uint64_t>::type;
+  constexpr B kExp = sizeof(T) == 4 ? (B)0x7f800000u : (B)0x7ff0000000000000ull;
+  constexpr int64_t kBlock = 4096;
+  int64_t b = 0;
+  for (; b + kBlock <= len; b += kBlock) {
+    B bad = 0;
+    for (int64_t i = 0; i < kBlock; ++i) {
+      B u;
+      std::memcpy(&u, v + b + i, sizeof u);
+      bad |= (B)((u & kExp) == kExp);
+    }
+    if (bad) return false;
+  }
+  B bad = 0;
+  for (; b < len; ++b) {
+    B u;
+    std::memcpy(&u, v + b, sizeof u);
+    bad |= (B)((u & kExp) == kExp);
+  }
+  return bad == 0;
 }
 
 // One launch of the core SVD kernel (single CTA), templated on the rank bucket.
