@@ -269,8 +269,12 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
 /* Releases a stream and its memory (synchronises). */
 isvd_status isvd_pool_release(isvd_pool_t p, int32_t stream_id);
 
-/* Queues ops (see above). All ops are validated (shape, bounds, finiteness) before any work is
- * queued; on error nothing is queued. payload is FP32, host or device memory. */
+/* Queues ops (see above). All ops are validated (stream, kind, shape, bounds, finite deltas)
+ * before any work is queued; on error nothing is queued. payload is FP32, host or device memory
+ * (payload_on_device). A host payload is also scanned for NaN/Inf first (ISVD_ENONFINITE, nothing
+ * queued; the scan reads the whole payload once). A device payload is not read by the host: a
+ * non-finite value there is seen by the kernels and reported as a sticky ISVD_ENONFINITE of that
+ * stream by the next isvd_pool_sync, as for device inputs of a single stream. */
 isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, const void* payload,
                              int64_t payload_len, int payload_on_device);
 
