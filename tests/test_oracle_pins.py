@@ -1,8 +1,8 @@
 """Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
 
 Each test checks the oracle against something other than itself: closed forms,
-brute-force LAPACK on explicitly formed matrices, identities stated in the paper,
-and special cases that reduce to a plain full SVD.
+brute-force LAPACK on explicitly formed matrices, a LAPACK-free one-sided Jacobi on the
+same matrices, identities stated in the paper, and special cases that reduce to a plain full SVD.
 """
 import json
 import math
@@ -284,3 +284,67 @@ def test_store_initial_subspace():
     assert o.metrics().angle > 1e-3
     o.refresh()
     assert o.metrics().angle < 1e-7
+
+
+# --- core singular values against a LAPACK-free Jacobi ------------------------
+
+def jacobi_singular_values(M, sweeps=80):
+    """Plain one-sided (Hestenes) Jacobi written out in Python, independent of LAPACK: rotate
+    column pairs of W = M until all pairs are orthogonal; the singular values are then the
+    column norms, sorted descending."""
+    W = np.array(M, dtype=np.float64, copy=True)
+    n = W.shape[1]
+    for _ in range(sweeps):
+        worst = 0.0
+        for a in range(n - 1):
+            for b in range(a + 1, n):
+                alpha = float(W[:, a] @ W[:, a])
+                beta = float(W[:, b] @ W[:, b])
+                gamma = float(W[:, a] @ W[:, b])
+                if gamma == 0.0 or abs(gamma) <= 1e-16 * math.sqrt(alpha * beta):
+                    continue
+                worst = max(worst, abs(gamma) / math.sqrt(alpha * beta))
+                zeta = (beta - alpha) / (2.0 * gamma)
+                t = math.copysign(1.0, zeta) / (abs(zeta) + math.sqrt(1.0 + zeta * zeta))
+                c = 1.0 / math.sqrt(1.0 + t * t)
+                s = c * t
+                wa, wb = W[:, a].copy(), W[:, b].copy()
+                W[:, a] = c * wa - s * wb
+                W[:, b] = s * wa + c * wb
+        if worst < 1e-15:
+            break
+    return np.sort(np.sqrt(np.sum(W * W, axis=0)))[::-1]
+
+
+def test_jacobi_reference_on_closed_form():
+    # diag(3, 1) rotated by orthogonal factors: singular values 3 and 1 whatever the rotations.
+    th, ph = 0.3, 1.1
+    Rl = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    Rr = np.array([[math.cos(ph), math.sin(ph)], [-math.sin(ph), math.cos(ph)]])
+    np.testing.assert_allclose(jacobi_singular_values(Rl @ np.diag([3.0, 1.0]) @ Rr), [3.0, 1.0], atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_update_spectra_match_lapack_free_jacobi(seed):
+    # Sections 2.2-2.3: the untruncated core's singular values are those of the explicitly formed
+    # updated matrix (stacked row, stacked column, or projected rank-one change), computed here by
+    # the Jacobi above rather than by LAPACK.
+    g = rng(70 + seed)
+    m, n, k = 7, 5, 3
+    U, s, V = truncated_svd(g.standard_normal((m, n)), k)
+    Ahat = (U * s) @ V.T
+    x = g.standard_normal(n)
+    _, sK, _, _, _, grew = row_append_update(U, s, V, x, 1e-10)
+    assert grew
+    ref = jacobi_singular_values(np.vstack([Ahat, x[None, :]]))[:k + 1]
+    np.testing.assert_allclose(sK, ref, rtol=0, atol=1e-12 * ref[0])
+    y = g.standard_normal(m)
+    sK2 = col_append_update(U, s, V, y, 1e-10)[1]
+    ref2 = jacobi_singular_values(np.hstack([Ahat, y[:, None]]))[:k + 1]
+    np.testing.assert_allclose(sK2, ref2, rtol=0, atol=1e-12 * ref2[0])
+    i, j, d = int(g.integers(m)), int(g.integers(n)), float(g.standard_normal())
+    s3 = rank_one_update(U, s, V, i, j, d)[1]
+    E = np.zeros((m, n))
+    E[i, j] = d
+    ref3 = jacobi_singular_values((U @ U.T) @ (Ahat + E) @ (V @ V.T))[:k]
+    np.testing.assert_allclose(s3, ref3, rtol=0, atol=1e-12 * ref3[0])
