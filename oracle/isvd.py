@@ -50,43 +50,44 @@ def truncated_svd(A: np.ndarray, k: int):
 
 
 def row_append_update(U, s, V, x, tol_rel):
-    """RowAppendUpdate, Algorithm A1 / Section 2.2 Steps 1-3 (no truncation here).
+    """Row append of Section 2.2 (Algorithm A1), before truncation.
 
-    Step 1 (Eq. row-residual): p = x^T V, z = x^T - p V^T, rho = ||z||.
-    Reading (tol): the paper's "small numerical threshold" is taken relative to the
-    row, tol = tol_rel * ||x||, so that only roundoff-sized residuals are dropped.
-    Step 2: K = [[Sigma, 0], [p, rho]] ((r+1) x (r+1)), full SVD K = U_K S' V_K^T.
-    Step 3: U' = blkdiag(U, 1) U_K,  V' = [V  z_hat] V_K.
-    Reading (rho <= tol): z_hat = 0 would put a zero column into V'; the update is
-    "rank-preserving", so the core is taken as the (r+1) x r matrix [[Sigma], [p]]
-    (equivalently rho = 0 with its zero singular value dropped) and V' = V V_K.
+    The appended matrix factors exactly through a small core: split x into its part in span(V),
+    with coordinates p = V^T x, and the residual z = x - V p of norm rho (Eq. row-residual).
+    Then [U S V^T; x^T] = blkdiag(U, 1) K [V, z/rho]^T with K the (r+1) x (r+1) lower arrow
+    matrix holding S on its diagonal, p^T as its last row and rho in the corner; an SVD of K,
+    K = W S' Z^T, gives the new factors blkdiag(U, 1) W and [V, z/rho] Z.
+
+    Reading (rank test): the residual is kept as a new direction only when rho exceeds
+    tol_rel * ||x||, a threshold relative to the row. Reading (residual dropped): the row then
+    lies in span(V) to rounding, z/rho is not a unit vector, and the factorisation is taken
+    with the (r+1) x r core [S; p^T] and right factor V Z (rank unchanged), which is the same
+    as keeping rho = 0 and discarding the zero singular value it produces.
 
     Returns (U', s', V', rho, p, rank_grew).
     """
     x = np.asarray(x, dtype=np.float64)
     r = s.size
-    p = V.T @ x                      # p = x^T V
-    z = x - V @ p                    # z = x^T - p V^T
-    rho = float(np.linalg.norm(z))   # rho = ||z||
-    tol = tol_rel * float(np.linalg.norm(x))
     m = U.shape[0]
-    Ubig = np.zeros((m + 1, r + 1))
-    Ubig[:m, :r] = U
-    Ubig[m, r] = 1.0                 # blkdiag(U, 1)
-    if rho > tol:
+    p = V.T @ x
+    z = x - V @ p
+    rho = float(np.linalg.norm(z))
+    left = np.zeros((m + 1, r + 1))          # blkdiag(U, 1)
+    left[:m, :r] = U
+    left[m, r] = 1.0
+    grew = rho > tol_rel * float(np.linalg.norm(x))
+    if grew:
         K = np.zeros((r + 1, r + 1))
         K[:r, :r] = np.diag(s)
         K[r, :r] = p
         K[r, r] = rho
-        UK, sK, VKt = np.linalg.svd(K)
-        Un = Ubig @ UK
-        Vn = np.hstack([V, (z / rho)[:, None]]) @ VKt.T
-        return Un, sK, Vn, rho, p, True
-    K = np.vstack([np.diag(s), p[None, :]])          # (r+1) x r
-    UK, sK, VKt = np.linalg.svd(K, full_matrices=False)
-    Un = Ubig @ UK
-    Vn = V @ VKt.T
-    return Un, sK, Vn, rho, p, False
+        right = np.hstack([V, (z / rho)[:, None]])
+        W, s_new, Zt = np.linalg.svd(K)
+    else:
+        K = np.vstack([np.diag(s), p[None, :]])
+        right = V
+        W, s_new, Zt = np.linalg.svd(K, full_matrices=False)
+    return left @ W, s_new, right @ Zt.T, rho, p, grew
 
 
 def col_append_update(U, s, V, y, tol_rel):
@@ -380,18 +381,3 @@ class OracleISVD:
             mt.refreshed = fire
             self.log.append(mt)
 
-
-def canonical(U, s, V):
-    """Sign/order canonical form: descending sigma, each (u_l, v_l) pair flipped so the
-    largest-|.| entry of u_l (lowest index on ties) is positive."""
-    U = np.array(U, dtype=np.float64, copy=True)
-    V = np.array(V, dtype=np.float64, copy=True)
-    s = np.array(s, dtype=np.float64, copy=True)
-    order = np.argsort(-s, kind="stable")
-    U, s, V = U[:, order], s[order], V[:, order]
-    for l in range(s.size):
-        idx = int(np.argmax(np.abs(U[:, l])))
-        if U[idx, l] < 0:
-            U[:, l] *= -1
-            V[:, l] *= -1
-    return U, s, V
