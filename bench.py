@@ -51,7 +51,7 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) of one launch from the ncu --set full capture summarised under
 # profiles/ (tick 1 of the default workload; later ticks differ by < 1%). Set to None whenever
 # the kernel changes until it is captured again.
-DRAM_TRAFFIC = {"k_pool_rotate<32>": 243461376}
+DRAM_TRAFFIC = {"k_pool_rotate<32>": 243461376, "k_pool_rotate_tc<32>": None}
 
 
 def measured_peaks():
@@ -314,7 +314,8 @@ def run_batched(args):
     ns = rng.integers(W["n_lo"], W["n_hi"] + 1, size=S)
     ks = rng.choice(np.asarray(W["ks"]), size=S)
     st = torch.cuda.Stream()
-    pool = pkg.Pool(k_max=int(max(W["ks"])), stream=st.cuda_stream)
+    pool = pkg.Pool(k_max=int(max(W["ks"])), stream=st.cuda_stream,
+                    flags=pkg.POOL_SIMT_ROTATIONS if args.simt_rotations else 0)
     t0 = time.perf_counter()
     ids, rows, payload_parts, offs = [], [], [], []
     for sidx in range(S):
@@ -446,8 +447,9 @@ def run_batched(args):
     dom = max((c for c in class_bytes if prof.get(c, (0.0, 0))[1] > 0), key=lambda c: class_bytes[c])
     dom_ms, dom_n = prof[dom]
     ach = class_bytes.get(dom, 0.0) / (dom_ms / dom_n * 1e6) if dom in class_bytes else 0.0
+    tc = "" if args.simt_rotations else "_tc"
     kernel_names = {"warp8": "k_pool_warp<8>", "warp16": "k_pool_warp<16>", "warp32": "k_pool_warp<32>",
-                    "rot8": "k_pool_rotate<8>", "rot16": "k_pool_rotate<16>", "rot32": "k_pool_rotate<32>",
+                    "rot8": "k_pool_rotate<8>", "rot16": f"k_pool_rotate{tc}<16>", "rot32": f"k_pool_rotate{tc}<32>",
                     "retry": "k_pool_retry<32>", "cta": "k_pool_tick"}
     out = {
         "metric": "iSVD updates/s and p50/p99 update latency at err ratio<=1.05 vs plain GPU form",
@@ -642,6 +644,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--streams", type=int, default=0)
     ap.add_argument("--plain-ticks", type=int, default=1)
+    ap.add_argument("--simt-rotations", action="store_true",
+                    help="batched workload: rotate on the FP32 pipes in every rank bucket")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

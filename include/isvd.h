@@ -238,12 +238,21 @@ typedef struct isvd_pool_ctx* isvd_pool_t;
 
 typedef struct {
   int32_t k_max;             /* rank capacity of every stream, 1..64 */
-  int32_t reserved;
+  int32_t flags;             /* bit set of ISVD_POOL_* below (0: defaults) */
   int64_t max_streams;       /* slot limit (0: unlimited) */
   int64_t hbm_budget_bytes;  /* admission budget for the streams' device memory (0: unlimited) */
   void* cuda_stream;         /* CUDA stream of all pool work (NULL: legacy default stream) */
   double tol_rel;            /* rank test (<= 0: 3e-6) */
+  int64_t orth_every;        /* loss-of-orthogonality monitor: every stream is checked after this many
+                                of its updates (0: 256; < 0: never); streams are staggered so that
+                                about 1/orth_every of them are checked per tick */
+  double orth_tol;           /* re-orthogonalise U or V when max|Q^T Q - I| exceeds it (<= 0: 1e-5) */
 } isvd_pool_config;
+
+/* isvd_pool_config.flags */
+#define ISVD_POOL_SIMT_ROTATIONS 1  /* rotate on the FP32 pipes in every rank bucket (default: the
+                                       tensor-core rotation with split-TF32 operands for buckets 16
+                                       and 32) */
 
 /* One op of a pool submit: kind 0 row append, 1 column append, 2 entry update (as isvd_event). */
 typedef struct {

@@ -61,8 +61,12 @@ class Metrics(C.Structure):
 
 
 class PoolConfig(C.Structure):
-    _fields_ = [("k_max", C.c_int32), ("reserved", C.c_int32), ("max_streams", C.c_int64),
-                ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double)]
+    _fields_ = [("k_max", C.c_int32), ("flags", C.c_int32), ("max_streams", C.c_int64),
+                ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double),
+                ("orth_every", C.c_int64), ("orth_tol", C.c_double)]
+
+
+POOL_SIMT_ROTATIONS = 1
 
 
 class PoolOp(C.Structure):
@@ -329,9 +333,10 @@ class _Borrowed(ISVD):
 class Pool:
     """Many independent FP32 streams updated by fused per-tick launches (isvd_pool_*)."""
 
-    def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0):
-        cfg = PoolConfig(k_max=k_max, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
-                         cuda_stream=stream or 0, tol_rel=tol_rel)
+    def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0, flags=0,
+                 orth_every=0, orth_tol=0.0):
+        cfg = PoolConfig(k_max=k_max, flags=flags, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
+                         cuda_stream=stream or 0, tol_rel=tol_rel, orth_every=orth_every, orth_tol=orth_tol)
         h = C.c_void_p()
         st = lib().isvd_pool_create(C.byref(cfg), C.byref(h))
         if st:

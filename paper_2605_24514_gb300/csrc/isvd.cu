@@ -15,6 +15,7 @@
 #include "../../include/isvd.h"
 #include "launch.cuh"
 #include "pool_kernels.cuh"
+#include "pool_reorth.cuh"
 #include "pool_warp.cuh"
 #include "refresh_kernels.cuh"
 #include "update_kernels.cuh"
@@ -40,6 +41,7 @@ struct isvd_ctx {
   int k_host = 0;
   double orth_tol = 1e-12;
   int64_t orth_every = 0, since_orth = 0;
+  int orth_on_device = 0;  // the batched path's monitor (DevState orth_u/v, reorths) runs this stream
   void* Uref = nullptr;
   int64_t m_ref = 0, uref_cap = 0;
   int r_ref = 0;
@@ -497,9 +499,9 @@ isvd_status gemm_tn(isvd_ctx* h, const T* X, int64_t ldx, int cx, const T* Y, in
   return ISVD_OK;
 }
 
-// Eigendecomposition of the FP64 Gram matrix: FP64 Jacobi for FP64 storage (rotations in shared
-// memory up to n = 80, beyond that in the n x n FP64 scratch vk), FP32 Jacobi with FP64
-// Rayleigh-quotient eigenvalues for FP32 storage.
+// Eigendecomposition of an FP64 symmetric matrix: FP64 Jacobi (rotations in shared memory up to
+// n = 80, beyond that in the n x n FP64 scratch vk), or (fp64 = 0) FP32 Jacobi with FP64
+// Rayleigh-quotient eigenvalues.
 template <typename T>
 isvd_status sym_eig(isvd_ctx* h, const double* G, int n, double* evals, double* evecs, int fp64, double* vk) {
   const int threads = core_threads(std::max(n - 1, 1));
@@ -607,7 +609,8 @@ isvd_status finish_side(isvd_ctx* h, T* Q, int64_t rows, int r, const double* si
 // columns (capped at 128 and min(m, n)), test matrix warm-started with the current V (the
 // maintained right subspace) and completed with Gaussian columns, q power iterations with
 // re-orthonormalisation between passes, then the small SVD of B = Q^T A through the Gram
-// B B^T = Z^T Z (Z = A^T Q). E_opt^2 = N_t - sum sigma^2.
+// B B^T = Z^T Z (Z = A^T Q). The tail energy is not formed here: the metrics take E_opt as the
+// residual ||A - U S V^T||_F of the computed factorisation (no N_t - sum sigma^2 cancellation).
 template <typename T>
 isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm) {
   const int64_t m = h->m, n = h->n, lda = h->col_cap;
@@ -649,7 +652,7 @@ isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, in
   double* GB = h->small + 3 * kSmall;
   double* evecs = h->small + 2 * kSmall;
   if ((s = gemm_tn<double>(h, h->Zd, l, l, h->Zd, l, l, n, GB))) return s;
-  if ((s = sym_eig<T>(h, GB, l, h->evals, evecs, sizeof(T) == 8, h->small + kSmall))) return s;
+  if ((s = sym_eig<T>(h, GB, l, h->evals, evecs, 1, h->small + kSmall))) return s;
   k_eig_to_factors<T><<<1, 256, 0, h->stream>>>(h->evals, evecs, l, kr, sig_o, h->inv, Rl2, l, h->scal + 3);
   CKL(h);
   RotSide su{};
@@ -669,21 +672,21 @@ isvd_status tsvd_randomized(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, in
   k_small_gemm_cast<double><<<(unsigned)((n * kr + 255) / 256), 256, 0, h->stream>>>(h->Zd, n, l, evecs, kr, nullptr,
                                                                                      h->Cbuf, kr);
   CKL(h);
-  if ((s = one_sided_finish<T, double>(h, h->Cbuf, kr, Vo, n, Uo, m, kr, sig_o))) return s;
-  k_tail_from_N<<<1, 32, 0, h->stream>>>(h->st, sig_o, kr, h->scal + 1);
-  CKL(h);
-  return ISVD_OK;
+  return one_sided_finish<T, double>(h, h->Cbuf, kr, Vo, n, Uo, m, kr, sig_o);
 }
 
 // Truncated SVD of the stored A_t at rank kr (Algorithm 1 "TruncatedSVD", Section 2.4):
-// Uo (m x kr, row stride ld), sig_o (kr), Vo (n x kr, row stride ld), and the tail energy
-// sum_{j > kr} s_j^2 in h->scal[1]. Exact path through the Gram matrix of the short side.
+// Uo (m x kr, row stride ld), sig_o (kr), Vo (n x kr, row stride ld); on the exact path (through
+// the Gram matrix of the short side) also the tail energy sum_{j > kr} s_j^2 in h->scal[1].
 template <typename T>
 isvd_status tsvd(isvd_ctx* h, int kr, T* Uo, double* sig_o, T* Vo, int warm = 1) {
   const int64_t m = h->m, n = h->n;
   const int64_t lda = h->col_cap;
   const T* A = (const T*)h->A;
-  const int fp64 = sizeof(T) == sizeof(double);
+  // The small symmetric eigenproblem runs in FP64 for both storage types: with FP32 Jacobi the
+  // eigenvectors of nearly equal eigenvalues (a noise bulk at the truncation boundary) were off by
+  // eps * ||G|| / gap, far above the FP32 path's tolerance.
+  const int fp64 = 1;
   if (std::min(m, n) > kKmaxLimit) return tsvd_randomized<T>(h, kr, Uo, sig_o, Vo, warm);
   isvd_status s;
   const int q = (int)std::min(m, n);
@@ -821,10 +824,10 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   mt->evr = ds.N > 0 ? ss / ds.N : NAN;
   mt->rho_last = ds.rho;
   mt->novelty_last = ds.novelty;
-  mt->orth_err_u = h->orth_err_u;
-  mt->orth_err_v = h->orth_err_v;
+  mt->orth_err_u = h->orth_on_device && ds.orth_runs > 0 ? ds.orth_u : h->orth_err_u;
+  mt->orth_err_v = h->orth_on_device && ds.orth_runs > 0 ? ds.orth_v : h->orth_err_v;
   mt->refreshes = h->refreshes;
-  mt->reorths = h->reorths;
+  mt->reorths = h->reorths + ds.reorths;
   mt->t_last = h->t_last;
   mt->core_sweeps = ds.sweeps;
   const double nan = std::nan("");
@@ -845,6 +848,16 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   if ((s = tsvd<T>(h, r, (T*)h->Uopt, h->sig_opt, (T*)h->Vopt))) return s;
   h->opt_t = h->t;
   h->opt_rank = r;
+  if (std::min(h->m, h->n) > kKmaxLimit) {
+    // Randomized path: E_opt = ||A - U_opt S_opt V_opt^T||_F of the computed rank-r factorisation,
+    // summed entry by entry in FP64 (an upper bound of the optimum that needs no tail spectrum).
+    CK(h, cudaMemsetAsync(h->scal + 1, 0, 8, h->stream));
+    dim3 grid((unsigned)((h->n + kResTile - 1) / kResTile), (unsigned)((h->m + kResTile - 1) / kResTile));
+    const size_t sm = (size_t)2 * std::max(r, 1) * (kResTile + 1) * sizeof(T);
+    k_resid_norm<T><<<grid, 256, sm, h->stream>>>((const T*)h->A, h->col_cap, h->m, h->n, (const T*)h->Uopt,
+                                                  (const T*)h->Vopt, h->ld, h->sig_opt, h->st, h->scal + 1, r);
+    CKL(h);
+  }
   double sc[2];
   CK(h, cudaMemcpyAsync(sc, h->scal, 16, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -870,7 +883,8 @@ template <typename T>
 isvd_status orth_err(isvd_ctx* h, const T* Q, int64_t rows, int r, double* err) {
   isvd_status s;
   double* B = h->small + 4 * kSmall;
-  if ((s = gemm_tn<T>(h, Q, h->ld, r, Q, h->ld, r, rows, B))) return s;
+  // Exact FP64 products: the measurement error stays far below the FP32 orthogonality level.
+  if ((s = gemm_tn<T>(h, Q, h->ld, r, Q, h->ld, r, rows, B, true))) return s;
   k_max_offident<<<1, 256, 0, h->stream>>>(B, r, h->scal + 2);
   CKL(h);
   CK(h, cudaMemcpyAsync(err, h->scal + 2, 8, cudaMemcpyDeviceToHost, h->stream));
@@ -907,6 +921,8 @@ isvd_status do_reorth(isvd_ctx* h, int force, double* eu, double* ev) {
   const int r = ds.r;
   if ((s = orth_err<T>(h, (const T*)h->U, h->m, r, &h->orth_err_u))) return s;
   if ((s = orth_err<T>(h, (const T*)h->V, h->n, r, &h->orth_err_v))) return s;
+  if (std::isnan(h->orth_err_u) || std::isnan(h->orth_err_v))
+    return fail(h, ISVD_ENONFINITE, "non-finite values in U or V (orthogonality monitor)");
   if (force || h->orth_err_u > h->orth_tol || h->orth_err_v > h->orth_tol) {
     for (int pass = 0; pass < 2; ++pass) {
       if ((s = cholqr_pass<T>(h, (T*)h->U, h->m, r))) return s;
@@ -1342,6 +1358,13 @@ const char* isvd_last_error(isvd_t h) { return h ? h->err.c_str() : "null handle
 
 struct isvd_pool_ctx {
   int kmax = 32, kb = 32;
+  int flags = 0;
+  int64_t orth_every = 256;  // <= 0: no monitor
+  double orth_tol = 1e-5;
+  PoolReorthOp* reorth_pinned = nullptr;  // per submit: the monitor's stream list of every tick
+  PoolReorthOp* reorth_dev = nullptr;
+  int64_t reorth_cap = 0;
+  int64_t reorth_runs = 0;
   cudaStream_t stream = nullptr;
   int64_t budget = 0, used = 0, max_streams = 0;
   double tol_rel = 3e-6;
@@ -1446,7 +1469,7 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
                                const int* block_op, int nblocks) {
   const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
-  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op);
+  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, !(p->flags & ISVD_POOL_SIMT_ROTATIONS));
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1486,6 +1509,9 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->budget = cfg->hbm_budget_bytes;
   p->max_streams = cfg->max_streams > 0 ? cfg->max_streams : (int64_t)1 << 30;
   p->tol_rel = cfg->tol_rel > 0 ? cfg->tol_rel : 3e-6;
+  p->flags = cfg->flags;
+  p->orth_every = cfg->orth_every == 0 ? 256 : cfg->orth_every;
+  p->orth_tol = cfg->orth_tol > 0 ? cfg->orth_tol : 1e-5;
   p->cfg.prec = ISVD_FP32;
   p->cfg.k_max = p->kmax;
   p->cfg.tol_rel = p->tol_rel;
@@ -1536,6 +1562,8 @@ void isvd_pool_destroy(isvd_pool_t p) {
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->chunks_dev) cudaFree(p->chunks_dev);
   if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
+  if (p->reorth_dev) cudaFree(p->reorth_dev);
+  if (p->reorth_pinned) cudaFreeHost(p->reorth_pinned);
   if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
   if (p->payload) cudaFree(p->payload);
   if (p->copied) cudaEventDestroy(p->copied);
@@ -1578,6 +1606,10 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   }
   p->streams[id] = h;
   p->bytes[id] = need;
+  // The batched monitor: streams start at staggered points of the cadence, so that admissions
+  // made together are not all checked in the same tick.
+  h->orth_on_device = 1;
+  h->since_orth = p->orth_every > 0 ? ((int64_t)id * 37) % p->orth_every : 0;
   if (p->s_gen.size() < p->streams.size()) {
     const size_t ns = p->streams.size();
     p->s_m.resize(ns);
@@ -1808,7 +1840,11 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     if ((s = ensure_cols(h, nn[sid] + 1))) return s;
   }
   std::vector<char> fused(nops, 0);
+  // Streams whose monitor is due, per tick (checked after that tick's updates).
+  std::vector<PoolReorthOp> reorth;
+  std::vector<int64_t> reorth_start(nticks + 1, 0);
   for (int32_t t = 0; t < nticks; ++t) {
+    reorth_start[t] = (int64_t)reorth.size();
     for (int64_t q = tick_start[t]; q < tick_start[t + 1]; ++q) {
       const int64_t e = order[q];
       const isvd_op& o = ops[e];
@@ -1835,6 +1871,24 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       if (o.kind == kRow) h->m += 1;
       else if (o.kind == kCol) h->n += 1;
       h->t += 1;
+      if (p->orth_every > 0 && ++h->since_orth >= p->orth_every) {
+        h->since_orth = 0;
+        reorth.push_back(PoolReorthOp{(float*)h->U, (float*)h->V, h->st, h->m, h->n, h->ld, 0});
+      }
+    }
+  }
+  reorth_start[nticks] = (int64_t)reorth.size();
+  if ((int64_t)reorth.size() > p->reorth_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->reorth_dev) cudaFree(p->reorth_dev);
+    if (p->reorth_pinned) cudaFreeHost(p->reorth_pinned);
+    p->reorth_dev = nullptr;
+    p->reorth_pinned = nullptr;
+    p->reorth_cap = std::max<int64_t>((int64_t)reorth.size(), 2 * p->reorth_cap);
+    if (cudaMalloc((void**)&p->reorth_dev, sizeof(PoolReorthOp) * (size_t)p->reorth_cap) != cudaSuccess ||
+        cudaMallocHost((void**)&p->reorth_pinned, sizeof(PoolReorthOp) * (size_t)p->reorth_cap) != cudaSuccess) {
+      p->reorth_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool monitor list");
     }
   }
   auto bucket_at = [&](int64_t z) { return (int)p->s_bucket[ops[order[z]].stream]; };
@@ -1884,6 +1938,12 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       cudaMemcpyAsync(p->chunks_dev, p->chunks_pinned, sizeof(int) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
           cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool descriptor copy");
+  if (!reorth.empty()) {
+    std::copy(reorth.begin(), reorth.end(), p->reorth_pinned);
+    if (cudaMemcpyAsync(p->reorth_dev, p->reorth_pinned, sizeof(PoolReorthOp) * reorth.size(), cudaMemcpyHostToDevice,
+                        p->stream) != cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool monitor list copy");
+  }
   cudaEventRecord(p->copied, p->stream);
   if (cudaMemsetAsync(p->retry_n, 0, sizeof(int) * (size_t)nticks, p->stream) != cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool retry counters");
@@ -1958,6 +2018,13 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
         }
       }
       q = q2;
+    }
+    const int64_t nre = reorth_start[t + 1] - reorth_start[t];
+    if (nre > 0) {
+      const cudaError_t e = pool_reorth_launch((int)nre, p->stream, p->reorth_dev + reorth_start[t], p->orth_tol);
+      if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool monitor launch: ") + cudaGetErrorString(e));
+      p->launches++;
+      p->reorth_runs += nre;
     }
     p->ticks++;
   }

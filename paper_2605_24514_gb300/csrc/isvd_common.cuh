@@ -38,6 +38,12 @@ struct DevState {
   double novelty;     // rho / ||x||
   unsigned int counter;   // last-block-done counter of the projection kernels
   unsigned int pad1;
+  // Loss-of-orthogonality monitor of the batched path: max|U^T U - I|, max|V^T V - I| at its last
+  // run and the re-orthogonalisations it performed.
+  double orth_u;
+  double orth_v;
+  int32_t reorths;
+  int32_t orth_runs;
 };
 
 // Optional phase timing (compile with -DISVD_CORE_TIMING): thread 0 of each CTA stores its

@@ -36,8 +36,14 @@ cudaError_t pool_retry_set_attr();
 // (kb = 8/16/32); scratch is the bucket run's first RotScratch<kb> record.
 cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
                              void* scratch, const int* chunks, int* block_op);
+// use_tc selects the tensor-core rotation (k_pool_rotate_tc, buckets 16 and 32).
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
-                               const int* chunks, const int* block_op);
+                               const int* chunks, const int* block_op, bool use_tc);
 cudaError_t pool_warp_set_attrs();
+
+// Batched loss-of-orthogonality monitor / re-orthogonalisation (k_pool_reorth), one CTA per
+// listed stream.
+struct PoolReorthOp;
+cudaError_t pool_reorth_launch(int count, cudaStream_t s, const PoolReorthOp* list, double tol);
 
 }  // namespace isvd

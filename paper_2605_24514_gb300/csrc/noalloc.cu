@@ -6,16 +6,21 @@
 // in a process whose allocator belongs to another framework. This entry point needs no
 // allocation: its scratch (the r x r FP64 Gram matrix and one result slot) lives in a file-scope
 // __device__ array of fixed size, which every GPU that loads the library keeps until exit.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/isvd.h"
 #include "isvd_common.cuh"
+#include "refresh_kernels.cuh"
 
 namespace {
 
+using isvd::k_gemm_tn;
+using isvd::k_max_offident;
+using isvd::kTnChunk;
+using isvd::kTnTile;
+
 constexpr int kNoAllocMaxR = ISVD_NOALLOC_MAX_R;
-constexpr int kNoAllocTile = 32;
-constexpr int kNoAllocChunk = 64;
 constexpr int kNoAllocMaxDevices = 64;
 
 // Scratch shared by every call: the Gram matrix (kNoAllocMaxR^2 doubles = 128 KiB) plus 32
@@ -24,69 +29,6 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxR * kNoAllo
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// G[a, b] += sum over a slice of rows of Q[row, a] Q[row, b] (G zeroed by the caller), products
-// summed in the storage type over runs of 16 rows and then in FP64.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gram_noalloc(const T* __restrict__ Q, int64_t ld, int r, int64_t rows,
-                                                      int64_t rows_per_split, double* __restrict__ G) {
-  __shared__ T xs[kNoAllocChunk][kNoAllocTile + 1];
-  __shared__ T ys[kNoAllocChunk][kNoAllocTile + 1];
-  const int a0 = blockIdx.x * kNoAllocTile, b0 = blockIdx.y * kNoAllocTile;
-  const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
-  int64_t r_end = r_begin + rows_per_split;
-  if (r_end > rows) r_end = rows;
-  const int t = threadIdx.x;
-  const int ta = t & 31, tb = t >> 5;
-  double acc[4] = {0, 0, 0, 0};
-  for (int64_t base = r_begin; base < r_end; base += kNoAllocChunk) {
-    for (int idx = t; idx < kNoAllocChunk * kNoAllocTile; idx += 256) {
-      const int rr = idx / kNoAllocTile, c = idx - rr * kNoAllocTile;
-      const int64_t row = base + rr;
-      const bool okr = row < r_end;
-      xs[rr][c] = (okr && a0 + c < r) ? Q[row * ld + a0 + c] : T(0);
-      ys[rr][c] = (okr && b0 + c < r) ? Q[row * ld + b0 + c] : T(0);
-    }
-    __syncthreads();
-    T part[4] = {0, 0, 0, 0};
-    for (int rr = 0; rr < kNoAllocChunk; ++rr) {
-      const T xv = xs[rr][ta];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) part[q] += xv * ys[rr][tb + 8 * q];
-      if ((rr & 15) == 15) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          acc[q] += (double)part[q];
-          part[q] = T(0);
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int a = a0 + ta, b = b0 + tb + 8 * q;
-    if (a < r && b < r && acc[q] != 0.0) atomicAdd(&G[(int64_t)a * r + b], acc[q]);
-  }
-}
-
-// *out = max |G - I| over the r x r matrix G.
-__global__ void k_offident_noalloc(const double* __restrict__ G, int r, double* __restrict__ out) {
-  __shared__ double red[32];
-  double mx = 0.0;
-  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-    const int a = idx / r, b = idx - a * r;
-    mx = fmax(mx, fabs(G[idx] - (a == b ? 1.0 : 0.0)));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
-    *out = m2;
-  }
-}
 
 // Device address of the scratch array on the current device, looked up once per device.
 isvd_status noalloc_scratch(void** out) {
@@ -113,16 +55,17 @@ isvd_status orth_error_impl(const T* Q, int64_t rows, int r, int64_t ld, double*
   double* G = static_cast<double*>(base);
   if (cudaMemsetAsync(G, 0, sizeof(double) * (size_t)r * r, st) != cudaSuccess) return ISVD_ECUDA;
   if (rows > 0) {
+    // The library's Gram kernel with exact FP64 products (row splits summed by FP64 atomics), as
+    // in the orthogonality monitor of isvd_reorthogonalize.
     const int64_t splits_target = 304;
     int64_t rps = (rows + splits_target - 1) / splits_target;
-    rps = ((rps + kNoAllocChunk - 1) / kNoAllocChunk) * kNoAllocChunk;
-    if (rps < kNoAllocChunk) rps = kNoAllocChunk;
-    const int tiles = (r + kNoAllocTile - 1) / kNoAllocTile;
-    dim3 grid((unsigned)tiles, (unsigned)tiles, (unsigned)((rows + rps - 1) / rps));
-    k_gram_noalloc<T><<<grid, 256, 0, st>>>(Q, ld, r, rows, rps, G);
+    rps = std::max<int64_t>(kTnChunk, (rps + kTnChunk - 1) / kTnChunk * kTnChunk);
+    const unsigned tiles = (unsigned)((r + kTnTile - 1) / kTnTile);
+    dim3 grid(tiles, tiles, (unsigned)((rows + rps - 1) / rps));
+    k_gemm_tn<T, true><<<grid, 256, 0, st>>>(Q, ld, r, Q, ld, r, rows, rps, G, r);
     if (cudaGetLastError() != cudaSuccess) return ISVD_ECUDA;
   }
-  k_offident_noalloc<<<1, 256, 0, st>>>(G, r, err_out);
+  k_max_offident<<<1, 256, 0, st>>>(G, r, err_out);
   if (cudaGetLastError() != cudaSuccess) return ISVD_ECUDA;
   return ISVD_OK;
 }

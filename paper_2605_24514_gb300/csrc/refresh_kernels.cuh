@@ -193,9 +193,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ A, int64_t lda, int64_t m, int64_t n,
                                                     const T* __restrict__ U, const T* __restrict__ V, int ld,
                                                     const double* __restrict__ sig, const DevState* st,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out, int r_fixed = -1) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int r = st->r;
+  const int r = r_fixed >= 0 ? r_fixed : st->r;
   T* Us = reinterpret_cast<T*>(smem);       // [r][kResTile + 1], scaled by sigma
   T* Vs = Us + (size_t)r * (kResTile + 1);  // [r][kResTile + 1]
   __shared__ double red[8];
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ A, int
 
 // Small helpers on r x r FP64 matrices (one CTA).
 // E = B - C^T C (tr = 0) or E = B - C C^T (tr = 1); C is rc x cc row-major; E is q x q.
-__global__ void k_angle_matrix(const double* __restrict__ B, const double* __restrict__ C, int rc, int cc, int tr,
+static __global__ void k_angle_matrix(const double* __restrict__ B, const double* __restrict__ C, int rc, int cc, int tr,
                                double* __restrict__ E) {
   const int q = tr ? rc : cc;
   for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
@@ -265,20 +265,24 @@ __global__ void k_angle_matrix(const double* __restrict__ B, const double* __res
   }
 }
 
-// max |B - I| over an r x r FP64 matrix into *out.
-__global__ void k_max_offident(const double* __restrict__ B, int r, double* __restrict__ out) {
+// NaN-propagating maximum: a NaN operand wins (fmax would drop it), so a factor holding NaN or
+// Inf reports a NaN orthogonality error instead of a small one.
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || isnan(b)) ? b : a; }
+
+// max |B - I| over an r x r FP64 matrix into *out (NaN if any entry is NaN).
+static __global__ void k_max_offident(const double* __restrict__ B, int r, double* __restrict__ out) {
   __shared__ double red[32];
   double mx = 0.0;
   for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
     const int a = idx / r, b = idx - a * r;
-    mx = fmax(mx, fabs(B[idx] - (a == b ? 1.0 : 0.0)));
+    mx = nan_max(mx, fabs(B[idx] - (a == b ? 1.0 : 0.0)));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = nan_max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = nan_max(m2, red[w]);
     *out = m2;
   }
 }
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(256) k_col_sumsq(const T* __restrict__ B, int6
 
 // Singular values from column norms, descending: sig[jj] = sqrt(sq[perm[jj]]), inv[jj] = 1 / sig[jj]
 // (0 for a zero column); ties keep the column order. One block.
-__global__ void k_sort_norms(const double* __restrict__ sq, int r, double* __restrict__ sig, int* __restrict__ perm,
+static __global__ void k_sort_norms(const double* __restrict__ sq, int r, double* __restrict__ sig, int* __restrict__ perm,
                              double* __restrict__ inv) {
   for (int j = threadIdx.x; j < r; j += blockDim.x) {  // NaN-safe defaults: no slot left unset
     perm[j] = j;
@@ -520,7 +524,7 @@ __global__ void k_small_gemm_cast(const double* __restrict__ Zd, int64_t rows, i
 }
 
 // Adds shift to the diagonal of an r x r FP64 matrix (shifted Cholesky-QR first pass).
-__global__ void k_add_diag(double* __restrict__ B, int r, double rel_shift) {
+static __global__ void k_add_diag(double* __restrict__ B, int r, double rel_shift) {
   __shared__ double tr;
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -529,14 +533,6 @@ __global__ void k_add_diag(double* __restrict__ B, int r, double rel_shift) {
   }
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) B[i * r + i] += rel_shift * tr + 1e-300;
-}
-
-// Tail energy of a randomized refresh: E_opt^2 = N_t - sum_{j < r} sig_j^2 (clamped at 0).
-__global__ void k_tail_from_N(const DevState* st, const double* __restrict__ sig, int r, double* __restrict__ out) {
-  double s = 0.0;
-  for (int j = threadIdx.x; j < r; j += 32) s += sig[j] * sig[j];
-  s = warp_sum(s);
-  if (threadIdx.x == 0) *out = fmax(st->N - s, 0.0);
 }
 
 }  // namespace isvd

@@ -6,8 +6,9 @@ random data, so that the CUDA path and the CPU oracle can be fed identical input
 The generator follows the factor-model description of the workloads (Section 5 uses a
 time x asset return panel; the synthetic stand-in used here has the same structure):
 
-* ``f`` latent factors with volatilities ``0.02 * 0.7**j`` (j = 0..f-1),
-  factor returns ``F[t, j] ~ N(0, (0.02*0.7**j)**2)``;
+* ``f`` latent factors with volatilities ``0.02 * 0.7**j`` (j = 0..f-1; the decay 0.7 can be
+  changed, e.g. to keep many factors above the noise), factor returns
+  ``F[t, j] ~ N(0, (0.02*0.7**j)**2)``;
 * loadings ``B[i, j] ~ N(0, 1) / sqrt(f)`` for every asset i;
 * idiosyncratic noise either ``scale * T_nu`` (unit-scale Student-t, default nu = 4,
   scale 0.01) or Gaussian with a given standard deviation;
@@ -38,6 +39,7 @@ class FactorModel:
     noise: str = "t"          # "t" (Student-t) or "gauss"
     noise_scale: float = 0.01
     nu: float = 4.0
+    vol_decay: float = 0.7
     rng: np.random.Generator = field(init=False, repr=False)
     B: np.ndarray = field(init=False, repr=False)
     F: np.ndarray = field(init=False, repr=False)
@@ -45,7 +47,7 @@ class FactorModel:
 
     def __post_init__(self):
         self.rng = np.random.Generator(np.random.PCG64(self.seed))
-        self.vol = 0.02 * 0.7 ** np.arange(self.f)
+        self.vol = 0.02 * self.vol_decay ** np.arange(self.f)
         self.B = self.rng.standard_normal((self.n, self.f)) / np.sqrt(self.f)
         self.F = np.zeros((64, self.f))
 
@@ -114,9 +116,9 @@ class EventStream:
 
 
 def make_panel(m0: int, n0: int, f: int, seed: int, noise: str = "t",
-               noise_scale: float = 0.01) -> tuple[np.ndarray, FactorModel]:
+               noise_scale: float = 0.01, vol_decay: float = 0.7) -> tuple[np.ndarray, FactorModel]:
     """Initial panel A0 (m0 x n0) and the generator that continues it."""
-    fm = FactorModel(n=n0, f=f, seed=seed, noise=noise, noise_scale=noise_scale)
+    fm = FactorModel(n=n0, f=f, seed=seed, noise=noise, noise_scale=noise_scale, vol_decay=vol_decay)
     return fm.rows(m0), fm
 
 

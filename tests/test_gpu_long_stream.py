@@ -1,0 +1,122 @@
+"""Long FP32 streams (10,000 updates) on the GPU against the FP64 oracle, through the C ABI.
+
+The FP32 path keeps U, V and A in FP32 and forms the core in float-float / FP64; over a long
+stream its rounding accumulates. After 10^4 mixed updates (70% row appends, 10% column appends,
+20% rank-1 entry updates) the largest principal angles between the GPU's and the oracle's U and V
+must stay within 1e-3 rad, and sigma and U S V^T within relative 1e-5 of the oracle's. The working
+rank is chosen at the factors of the model so that the subspaces being compared are well defined
+(a clear gap after sigma_k); the single stream runs its loss-of-orthogonality monitor at the
+default cadence, the pool stream runs the pool kernels.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_24514_gb300 import streams
+
+pytestmark = pytest.mark.gpu
+
+N_EVENTS = 10_000
+
+
+@pytest.fixture(scope="module")
+def isvd():
+    from paper_2605_24514_gb300 import build
+    build.build()
+    import paper_2605_24514_gb300 as pkg
+    return pkg
+
+
+def max_angle(Q1, Q2):
+    """Largest principal angle between span(Q1) and span(Q2) (orthonormalised first), as the
+    arcsine of ||(I - P1) Q2||_2 (accurate for small angles)."""
+    Q1, _ = np.linalg.qr(np.asarray(Q1, dtype=np.float64))
+    Q2, _ = np.linalg.qr(np.asarray(Q2, dtype=np.float64))
+    R = Q2 - Q1 @ (Q1.T @ Q2)
+    return float(np.arcsin(min(1.0, np.linalg.norm(R, 2))))
+
+
+# (seed, factors = k, noise scale, factor-volatility decay): one stream per rank bucket of the
+# batched kernels (8: FP32-pipe rotation; 16 and 32: tensor-core rotation), each with a clear gap
+# after sigma_k.
+POOL_STREAMS = [(202, 8, 1e-3, 0.7), (303, 12, 1e-4, 0.7), (404, 24, 1e-3, 0.95)]
+
+
+def _stream(seed, f=8, noise=1e-3, decay=0.7):
+    A0, fm = streams.make_panel(200, 60, f, seed, noise_scale=noise, vol_decay=decay)
+    ev = streams.make_events(fm, 200, N_EVENTS, mix=(0.7, 0.1, 0.2), seed=seed + 1)
+    return A0.astype(np.float32), ev
+
+
+def _oracle_run(A0, ev, k, factors):
+    o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=factors)
+    for e in range(len(ev)):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+        else:
+            o.apply(kd, ev.vector(e).astype(np.float32).astype(np.float64))
+    return o
+
+
+def _compare(U, s, V, o, what):
+    assert s.size == o.r, what
+    np.testing.assert_allclose(s, o.s, rtol=0, atol=1e-5 * o.s[0], err_msg=what)
+    R = (U.astype(np.float64) * s) @ V.astype(np.float64).T
+    Ro = o.reconstruction()
+    assert np.linalg.norm(R - Ro) <= 1e-5 * np.linalg.norm(Ro), what
+    assert max_angle(U, o.U) <= 1e-3, what
+    assert max_angle(V, o.V) <= 1e-3, what
+    # the gap that makes the comparison meaningful
+    full = np.linalg.svd(o.A_view(), compute_uv=False)
+    assert full[o.r] < 0.7 * full[o.r - 1], what
+
+
+def test_single_stream_fp32_10k_updates(isvd):
+    A0, ev = _stream(101)
+    k = 8
+    f = oracle.truncated_svd(A0.astype(np.float64), k)
+    g = isvd.ISVD(A0, k, prec=isvd.FP32, factors=f)
+    g.apply_events(ev)
+    U, s, V = g.factors()
+    o = _oracle_run(A0, ev, k, f)
+    assert g.shape()[:2] == (o.m, o.n) == (int(ev.m_after[-1]), int(ev.n_after[-1]))
+    assert g.metrics(full=False)["reorths"] >= 1
+    _compare(U, s, V, o, "single stream")
+
+
+def test_pool_streams_fp32_10k_updates(isvd):
+    """Three streams (rank buckets 8, 16, 32) in one pool, 10^4 updates each, every tick holding
+    one update of every stream; the pool's staggered loss-of-orthogonality monitor runs."""
+    data = []
+    pool = isvd.Pool(k_max=32)
+    for seed, k, noise, decay in POOL_STREAMS:
+        A0, ev = _stream(seed, f=k, noise=noise, decay=decay)
+        f = oracle.truncated_svd(A0.astype(np.float64), k)
+        data.append((A0, ev, k, f, pool.admit(A0, k, factors=f)))
+    ops, chunks, pos = [], [], 0
+    for e in range(N_EVENTS):
+        for A0, ev, k, f, sid in data:
+            kd = int(ev.kind[e])
+            if kd == streams.ENTRY:
+                ops.append((sid, kd, int(ev.i[e]), int(ev.j[e]), float(ev.delta[e]), 0, 0))
+            else:
+                v = ev.vector(e).astype(np.float32)
+                ops.append((sid, kd, 0, 0, 0.0, pos, v.size))
+                chunks.append(v)
+                pos += v.size
+    pool.submit(ops, np.concatenate(chunks))
+    pool.sync()
+    for A0, ev, k, f, sid in data:
+        h = pool.stream(sid)
+        U, s, V = h.factors()
+        o = _oracle_run(A0, ev, k, f)
+        _compare(U, s, V, o, f"pool stream k={k}")
+        # The monitor measured both sides at its cadence (about 10^4 / 256 times) and kept them
+        # within a few times its tolerance of 1e-5 in between.
+        mt = h.metrics(full=False)
+        assert 0.0 < mt["orth_err_u"] < 1e-4 and 0.0 < mt["orth_err_v"] < 1e-4, k
+        for Q in (U, V):
+            Q = Q.astype(np.float64)
+            assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 5e-5, k
+    pool.close()

@@ -275,3 +275,33 @@ def test_pool_warp_ranks_and_sides(isvd, k):
     A = pool.stream(sid).matrix()
     np.testing.assert_allclose(A, o.A_view(), rtol=0, atol=1e-6)
     pool.close()
+
+
+@pytest.mark.parametrize("k", [9, 16, 21, 32])
+def test_pool_tensor_core_rotation_matches_fp32_pipes(isvd, k):
+    """The tensor-core rotation (split-TF32 operands, rank buckets 16 and 32) against the FP32-pipe
+    rotation and the oracle, on sides that span several 256-row tiles with ragged tails (rows and
+    columns interleaved, so both the projection side with z_hat and the other side are rotated)."""
+    A0, fm = streams.make_panel(613, 301, 40, seed=60 + k)
+    A0 = A0.astype(np.float32)
+    f = oracle.truncated_svd(A0.astype(np.float64), k)
+    ev = streams.make_events(fm, 613, 10, mix=(0.6, 0.4, 0.0), seed=80 + k)
+    pools = [isvd.Pool(k_max=32), isvd.Pool(k_max=32, flags=isvd.POOL_SIMT_ROTATIONS)]
+    sids = [p.admit(A0, k, factors=f) for p in pools]
+    o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+    for e in range(len(ev)):
+        v = ev.vector(e).astype(np.float32)
+        for p, sid in zip(pools, sids):
+            p.submit([(sid, int(ev.kind[e]), 0, 0, 0.0, 0, v.size)], v)
+        o.apply(int(ev.kind[e]), v.astype(np.float64))
+    for p, sid in zip(pools, sids):
+        p.sync()
+        _check_stream(p, sid, o)
+    (U1, s1, V1), (U2, s2, V2) = (p.stream(sid).factors() for p, sid in zip(pools, sids))
+    nrm = np.linalg.norm(o.reconstruction())
+    assert np.linalg.norm(recon(U1, s1, V1) - recon(U2, s2, V2)) <= 1e-5 * nrm
+    for U, V in ((U1, V1), (U2, V2)):
+        assert np.abs(U.T.astype(np.float64) @ U - np.eye(U.shape[1])).max() < 1e-5
+        assert np.abs(V.T.astype(np.float64) @ V - np.eye(V.shape[1])).max() < 1e-5
+    for p in pools:
+        p.close()
