@@ -309,13 +309,17 @@ def run_batched(args):
     S = args.streams or W["streams"]
     K, Wm = args.steps, args.warmup
     plain_ticks = args.plain_ticks
-    T = Wm + K + plain_ticks + (K if not args.no_e2e else 0)
+    n_lat = args.lat_ticks
+    t_lat = Wm + K
+    t_plain = t_lat + n_lat
+    t_e2e = t_plain + (plain_ticks + 1 if plain_ticks > 0 else 0)
+    T = t_e2e + (K if not args.no_e2e else 0)
     rng = np.random.Generator(np.random.PCG64(rank_seed(rank)))
     ns = rng.integers(W["n_lo"], W["n_hi"] + 1, size=S)
     ks = rng.choice(np.asarray(W["ks"]), size=S)
     st = torch.cuda.Stream()
     pool = pkg.Pool(k_max=int(max(W["ks"])), stream=st.cuda_stream,
-                    flags=pkg.POOL_SIMT_ROTATIONS if args.simt_rotations else 0)
+                    flags=pkg.POOL_COMPLETIONS | (pkg.POOL_SIMT_ROTATIONS if args.simt_rotations else 0))
     t0 = time.perf_counter()
     ids, rows, payload_parts, offs = [], [], [], []
     for sidx in range(S):
@@ -388,6 +392,7 @@ def run_batched(args):
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     prof = pool.profile_read()
+    host_phases, host_n = pool.host_profile()
     pool.profile(False)
     launches = pool.launches - l0
     tick_ms = np.array([a.elapsed_time(b_) for a, b_ in evs])
@@ -395,48 +400,84 @@ def run_batched(args):
     pool.sync()
     ms = reduce_max(ms, world)
     value = world * K * S / (ms / 1e3)
-    # Plain GPU form: the same streams, next ticks, one single-stream launch sequence per stream.
-    handles = [pool.stream(i) for i in ids]
+    # Update latency: every update of a tick completes with it, so the latency of an update
+    # submitted at a tick boundary is that tick's device time; L more ticks, each timed alone.
+    lat_ms = []
+    for t in range(t_lat, t_lat + n_lat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        tick_dev(t)
+        e1.record(st)
+        lat_ms.append((e0, e1))
     torch.cuda.synchronize()
-    tp0 = time.perf_counter()
-    pe0 = torch.cuda.Event(enable_timing=True)
-    pe1 = torch.cuda.Event(enable_timing=True)
-    pe0.record(st)
-    torch.cuda.nvtx.range_push("plain")
-    for t in range(Wm + K, Wm + K + plain_ticks):
+    lat_ms = np.array([a.elapsed_time(b_) for a, b_ in lat_ms])
+    while pool.poll().size:                       # drop the records of the ticks so far
+        pass
+    # Plain GPU form: the same streams, next ticks, one single-stream launch sequence per stream
+    # (one untimed warm-up tick, then plain_ticks timed ones).
+    handles = [pool.stream(i) for i in ids]
+
+    def plain_tick(t):
         base = t * tick_len
         for sidx in range(S):
             off = base + int(starts[sidx])
-            x = pay_dev[off:off + int(ns[sidx])]
-            handles[sidx].append_row(x)
-    pe1.record(st)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    plain_value = plain_ticks * S / (pe0.elapsed_time(pe1) / 1e3) if plain_ticks > 0 else None
+            handles[sidx].append_row(pay_dev[off:off + int(ns[sidx])])
+
+    plain_value, plain_spread = None, None
+    if plain_ticks > 0:
+        plain_tick(t_plain)
+        torch.cuda.synchronize()
+        pms = []
+        torch.cuda.nvtx.range_push("plain")
+        for t in range(t_plain + 1, t_plain + 1 + plain_ticks):
+            pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pe0.record(st)
+            plain_tick(t)
+            pe1.record(st)
+            pms.append((pe0, pe1))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        pms = np.array([a.elapsed_time(b_) for a, b_ in pms])
+        plain_value = plain_ticks * S / (float(pms.sum()) / 1e3)
+        plain_spread = [round(float(pms.min()), 2), round(float(pms.max()), 2)]
     e2e = None
     if not args.no_e2e:
-        base_t = Wm + K + plain_ticks
-        pinned = torch.from_numpy(payload[base_t * tick_len:(base_t + K) * tick_len]).pin_memory()
+        # End to end through the C ABI: each tick's payload comes from pinned host memory, and each
+        # tick's results go back to the host: every stream's singular values (one gather, one copy)
+        # and every op's completion record. Ticks are pipelined: tick q+1 is submitted before the
+        # results of tick q are read.
+        pinned = torch.from_numpy(payload[t_e2e * tick_len:(t_e2e + K) * tick_len]).pin_memory()
+        sig_out = [torch.empty((pool.slots, 32), dtype=torch.float64).pin_memory() for _ in range(2)]
         pool.sync()
+        while pool.poll().size:
+            pass
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
-        d2h = 0
+        n_rec = 0
         for q in range(K):
             seg = pinned[q * tick_len:(q + 1) * tick_len]
             pool.submit_raw(ops, S, seg.data_ptr(), tick_len, 0)
-            sig = handles[0].sigma()
-            d2h += sig.nbytes
-        torch.cuda.synchronize()
+            pool.gather_sigma(32, out=sig_out[q % 2].numpy())
+            n_rec += pool.poll().size
+        pool.sync()
+        while True:
+            got = pool.poll().size
+            if not got:
+                break
+            n_rec += got
         el = reduce_max(time.perf_counter() - t0, world)
-        e2e = {"value": world * K * S / el, "unit": "updates/s", "h2d_bytes_per_step": int(tick_len * 4 + S * 48),
-               "d2h_bytes_per_step": int(d2h // K)}
-    # Accuracy gate: error ratio (Section 2.5) of a sample of streams after the timed ticks.
-    ratios, sweeps = [], []
-    for sidx in range(0, S, max(1, S // 8)):
-        mt = handles[sidx].metrics(full=True)
-        ratios.append(mt["frob_ratio"])
-    for sidx in range(0, S, max(1, S // 256)):
-        sweeps.append(handles[sidx].metrics(full=False)["core_sweeps"])
+        assert n_rec == K * S, (n_rec, K * S)
+        d2h = pool.slots * 32 * 8 + S * 48
+        e2e = {"value": world * K * S / el, "unit": "updates/s",
+               "h2d_bytes_per_step": int(tick_len * 4 + S * 136), "d2h_bytes_per_step": int(d2h),
+               "results": "all streams' sigma (gather, one D2H copy) and one completion record per update, per tick"}
+    # Error ratio (Section 2.5) of a sample of streams after all ticks; the CPU-baseline leg replays
+    # the same streams through the oracle and compares.
+    sample_ids = list(range(min(S, args.acc_streams)))
+    gpu_ratios = [handles[sidx].metrics(full=True)["frob_ratio"] for sidx in sample_ids]
+    sweeps = [handles[sidx].metrics(full=False)["core_sweeps"] for sidx in range(0, S, max(1, S // 256))]
     if rank != 0:
         return None
     peak, peak_src = measured_peaks()
@@ -460,13 +501,17 @@ def run_batched(args):
                    "k_mix": {str(k): int(np.sum(ks == k)) for k in W["ks"]},
                    "form": "per tick and rank bucket (8/16/32, concurrent streams): a warp-per-update projection + core launch and a row-parallel rotation launch; one hand-back launch",
                    "plain_form_updates_per_s": round(plain_value, 1) if plain_value else None,
+                   "plain_form_ticks": plain_ticks, "plain_form_tick_ms_min_max": plain_spread,
                    "speedup_vs_plain": round(value / plain_value, 2) if plain_value else None,
                    "l2": "working set per tick larger than L2 (no flush needed)",
-                   "latency_us": {"p50": round(float(np.percentile(tick_ms, 50)) * 1e3, 1),
-                                  "p99": round(float(np.percentile(tick_ms, 99)) * 1e3, 1),
-                                  "note": "an update completes with its tick"},
-                   "err_ratio_sample_max": round(float(np.nanmax(ratios)), 5) if ratios else None,
+                   "latency_us": {"p50": round(float(np.percentile(lat_ms, 50)) * 1e3, 1),
+                                  "p99": round(float(np.percentile(lat_ms, 99)) * 1e3, 1),
+                                  "max": round(float(lat_ms.max()) * 1e3, 1), "ticks": int(lat_ms.size),
+                                  "note": "device time of a tick, measured alone; every update of a tick "
+                                          "completes with it"},
+                   "err_ratio_gpu_sample": [round(float(r), 6) for r in gpu_ratios],
                    "host_submit_us_per_tick": round(float(np.mean(host_s)) * 1e6, 1),
+                   "host_submit_phases_us": {k: round(v / max(host_n, 1), 1) for k, v in host_phases.items()},
                    "core_fast_path_frac": round(float(np.mean(np.asarray(sweeps) >= 100)), 4) if sweeps else None,
                    "core_corrected_weights_frac": round(float(np.mean(np.asarray(sweeps) == 102)), 4) if sweeps else None,
                    "setup_s": round(setup_s, 1), "parallelism": "replicas" if world > 1 else "streams in one pool"},
@@ -483,12 +528,20 @@ def run_batched(args):
     }
     pool.close()
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline_batched(args, budget_s=args.cpu_budget)
+        cb, orc_ratios = cpu_baseline_batched(args, T, sample_ids)
+        out["cpu_baseline"] = cb
+        rel = [abs(g / o - 1.0) for g, o in zip(gpu_ratios, orc_ratios)]
+        out["config"]["accuracy"] = {
+            "err_ratio_oracle_sample": [round(float(r), 6) for r in orc_ratios],
+            "max_rel_diff_vs_oracle": float(max(rel)) if rel else None,
+            "ok": bool(all(np.isfinite(gpu_ratios)) and max(gpu_ratios) <= 1.05 and max(rel) <= 0.01),
+            "rule": "every sampled ratio finite and <= 1.05, and within 1% of the oracle's on the same stream"}
     return out
 
 
 def _batched_sample(args, n_streams, ticks):
-    """Streams of the batched workload for the CPU oracle (same generator, same seeds)."""
+    """Streams of the batched workload for the CPU oracle (same generator, same seeds, the same
+    rows: a stream's rows are drawn as one block of ``ticks`` rows, as on the GPU side)."""
     W = WORKLOADS["batched-4096"]
     rng = np.random.Generator(np.random.PCG64(rank_seed(0)))
     S = args.streams or W["streams"]
@@ -503,25 +556,22 @@ def _batched_sample(args, n_streams, ticks):
     return out
 
 
-def cpu_baseline_batched(args, budget_s=15.0):
-    """The oracle on a time-bounded sample of the batched workload: ticks over the first streams."""
+def cpu_baseline_batched(args, ticks, sample_ids):
+    """The oracle on a sample of the batched workload: the first streams, every tick the GPU ran
+    (in tick order); returns the timing and the oracle's error ratio of each sampled stream."""
     import oracle
-    data = _batched_sample(args, 64, 8)
+    data = _batched_sample(args, len(sample_ids), ticks)
     engines = [oracle.OracleISVD(A0, k, tol_rel=3e-6) for A0, _, k in data]
     t0 = time.perf_counter()
-    n = 0
-    for t in range(8):
+    for t in range(ticks):
         for (A0, rows, k), o in zip(data, engines):
             o.append_row(rows[t])
-            n += 1
-            if time.perf_counter() - t0 > budget_s:
-                break
-        if time.perf_counter() - t0 > budget_s:
-            break
     el = time.perf_counter() - t0
-    return {"value": round(n / el, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
-            "sample": f"{n} row appends over the first {len(data)} streams of the same workload "
-                      f"(tick order, time budget {budget_s:.0f} s)"}
+    n = ticks * len(data)
+    ratios = [o.metrics().frob_ratio for o in engines]
+    return ({"value": round(n / el, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
+             "sample": f"{n} row appends: the first {len(data)} streams of the same workload over all {ticks} "
+                       f"ticks the GPU ran, in tick order"}, ratios)
 
 
 def oracle_policy(W):
@@ -643,7 +693,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--streams", type=int, default=0)
-    ap.add_argument("--plain-ticks", type=int, default=1)
+    ap.add_argument("--plain-ticks", type=int, default=3)
+    ap.add_argument("--lat-ticks", type=int, default=100)
+    ap.add_argument("--acc-streams", type=int, default=8)
     ap.add_argument("--simt-rotations", action="store_true",
                     help="batched workload: rotate on the FP32 pipes in every rank bucket")
     args = ap.parse_args()

@@ -230,14 +230,20 @@ const char* isvd_status_string(isvd_status s);
 /* --- batched pool of independent streams ---------------------------------------------------
  * Many streams (each the single-stream engine above, FP32 bulk) share one CUDA stream. A submit
  * takes an ordered list of ops; ops of the same stream are applied in list order, ops of different
- * streams are grouped into "ticks" (at most one op per stream) and each tick is ONE fused kernel
- * launch in which one CTA performs one whole update (projection, core SVD, rotations, dense-A and
- * N_t bookkeeping) of one stream. Streams are admitted under an HBM budget. The pool path runs no
- * refresh policy; isvd_pool_stream gives the stream's handle for refresh, metrics and reads. */
+ * streams are grouped into "ticks" (at most one op per stream). Per tick, the appends of rank
+ * buckets 8, 16 and 32 run as one launch per bucket of a warp-per-update kernel (projection with
+ * CGS2, core SVD, dense-A and N_t bookkeeping) followed by one launch of a row-parallel rotation
+ * kernel per bucket (tensor cores for buckets 16 and 32), the buckets on concurrent CUDA streams;
+ * entry updates, bucket 64 and the updates the warp kernel hands back take a CTA-per-update kernel.
+ * The launch count per tick does not depend on the number of streams. Streams are admitted under an
+ * HBM budget; a staggered loss-of-orthogonality monitor re-orthonormalises streams as needed. The
+ * pool path runs no refresh policy; isvd_pool_stream gives the stream's handle for refresh, metrics
+ * and reads. */
 typedef struct isvd_pool_ctx* isvd_pool_t;
 
 typedef struct {
-  int32_t k_max;             /* rank capacity of every stream, 1..64 */
+  int32_t k_max;             /* largest admitted rank, 1..128 (streams above 64 take the
+                                single-stream kernels, in order) */
   int32_t flags;             /* bit set of ISVD_POOL_* below (0: defaults) */
   int64_t max_streams;       /* slot limit (0: unlimited) */
   int64_t hbm_budget_bytes;  /* admission budget for the streams' device memory (0: unlimited) */
@@ -247,12 +253,35 @@ typedef struct {
                                 of its updates (0: 256; < 0: never); streams are staggered so that
                                 about 1/orth_every of them are checked per tick */
   double orth_tol;           /* re-orthogonalise U or V when max|Q^T Q - I| exceeds it (<= 0: 1e-5) */
+  int64_t rank_every;        /* adaptive rank (Section 3, Eq. evr-rank-rule read as a growth rule):
+                                after every rank_every-th update of a stream (t mod rank_every == 0),
+                                k <- min(k + 1, capacity) if sum sigma^2 / N_t < tau_evr; the new
+                                component arrives with the stream's next append that keeps its
+                                residual. 0: off. The capacity is the stream's rank bucket (8, 16,
+                                32, 64 or 128, the smallest holding the admitted k) capped by k_max. */
+  double tau_evr;            /* EVR target of the adaptive rank rule */
 } isvd_pool_config;
 
 /* isvd_pool_config.flags */
 #define ISVD_POOL_SIMT_ROTATIONS 1  /* rotate on the FP32 pipes in every rank bucket (default: the
                                        tensor-core rotation with split-TF32 operands for buckets 16
                                        and 32) */
+#define ISVD_POOL_COMPLETIONS 2     /* every op of a submit leaves a completion record for
+                                       isvd_pool_poll */
+
+/* Completion record of one pool op (ISVD_POOL_COMPLETIONS). */
+typedef struct {
+  int64_t seq;        /* pool-wide sequence number: the ops of all submits are numbered from 0 in the
+                         order they were given (submit by submit, op by op) */
+  int32_t stream;     /* stream id */
+  int32_t kind;       /* 0 row append, 1 column append, 2 entry update */
+  int32_t status;     /* ISVD_OK, or the stream's sticky device status after the op */
+  int32_t r;          /* maintained rank after the op */
+  double rho;         /* residual norm of an append, Eq. (row-residual); 0 for an entry update */
+  double sigma_max;   /* largest singular value after the op */
+  uint64_t done_ns;   /* device clock (%globaltimer, ns) when the record was written, right after the
+                         op's tick */
+} isvd_completion;
 
 /* One op of a pool submit: kind 0 row append, 1 column append, 2 entry update (as isvd_event). */
 typedef struct {
@@ -290,6 +319,25 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
 /* Waits for the pool's work; reports sticky device errors of any stream. */
 isvd_status isvd_pool_sync(isvd_pool_t p);
 
+/* Completion records (pool created with ISVD_POOL_COMPLETIONS): copies up to cap records of ops
+ * whose work has finished on the device and that no earlier poll returned into out, and their
+ * number into *nout. Never waits. Records come submit by submit; within a submit, tick by tick
+ * (a stream's ops in its order), and within a tick in the pool's launch order (seq identifies the
+ * op). Records are kept (in pinned host memory) until polled. ISVD_EINVAL if the pool was created
+ * without ISVD_POOL_COMPLETIONS; ISVD_ECUDA if a CUDA call failed. */
+isvd_status isvd_pool_poll(isvd_pool_t p, isvd_completion* out, int64_t cap, int64_t* nout);
+
+/* Number of stream slots (one past the largest stream id ever admitted). */
+int64_t isvd_pool_slots(isvd_pool_t p);
+
+/* Singular values of every slot in one array: out[s * ld + c] = sigma_c of stream s for
+ * c < min(r_s, ld), zero elsewhere (released slots are all zero); out holds isvd_pool_slots(p) * ld
+ * doubles, device memory (to_device = 1) or host memory. The gather is queued on the pool's CUDA
+ * stream after all submitted work: a device or pinned host buffer is filled asynchronously (ready
+ * when the stream reaches it, e.g. after isvd_pool_sync); a pageable host buffer is filled before
+ * the call returns. ld >= 1. */
+isvd_status isvd_pool_gather_sigma(isvd_pool_t p, int32_t ld, double* out, int to_device);
+
 /* The single-stream handle of a pool stream (owned by the pool; do not destroy), or NULL. */
 isvd_t isvd_pool_stream(isvd_pool_t p, int32_t stream_id);
 
@@ -316,6 +364,11 @@ isvd_status isvd_pool_profile(isvd_pool_t p, int enable);
 /* Synchronizes the pool and writes, per launch class, the summed device time in ms (ms_out) and
  * the number of launches (launches_out), each an array of n <= ISVD_POOL_NUM_KCLASS entries. */
 isvd_status isvd_pool_profile_read(isvd_pool_t p, double* ms_out, int64_t* launches_out, int n);
+/* Host wall time (microseconds) that isvd_pool_submit spent since profiling was enabled, by phase:
+ * [0] validating the ops, [1] ordering them into ticks and rank buckets, [2] staging descriptors
+ * (including any wait for the copy of two submits ago), [3] enqueueing copies and launches;
+ * n <= 4 entries. *submits (may be NULL) receives the number of submits counted. */
+isvd_status isvd_pool_host_profile(isvd_pool_t p, double* us_out, int n, int64_t* submits);
 
 /* --- allocation-free orthogonality measurement ----------------------------------------------
  * The paper has no counterpart: this is a library service for callers that cannot allocate

@@ -63,10 +63,17 @@ class Metrics(C.Structure):
 class PoolConfig(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("flags", C.c_int32), ("max_streams", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double),
-                ("orth_every", C.c_int64), ("orth_tol", C.c_double)]
+                ("orth_every", C.c_int64), ("orth_tol", C.c_double), ("rank_every", C.c_int64),
+                ("tau_evr", C.c_double)]
 
 
 POOL_SIMT_ROTATIONS = 1
+POOL_COMPLETIONS = 2
+
+
+class Completion(C.Structure):
+    _fields_ = [("seq", C.c_int64), ("stream", C.c_int32), ("kind", C.c_int32), ("status", C.c_int32),
+                ("r", C.c_int32), ("rho", C.c_double), ("sigma_max", C.c_double), ("done_ns", C.c_uint64)]
 
 
 class PoolOp(C.Structure):
@@ -122,6 +129,10 @@ _SIGS = {
     "isvd_pool_last_error": (C.c_char_p, [C.c_void_p]),
     "isvd_pool_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "isvd_pool_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
+    "isvd_pool_host_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int64)]),
+    "isvd_pool_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "isvd_pool_slots": (C.c_int64, [C.c_void_p]),
+    "isvd_pool_gather_sigma": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int]),
 }
 
 
@@ -334,9 +345,10 @@ class Pool:
     """Many independent FP32 streams updated by fused per-tick launches (isvd_pool_*)."""
 
     def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0, flags=0,
-                 orth_every=0, orth_tol=0.0):
+                 orth_every=0, orth_tol=0.0, rank_every=0, tau_evr=0.9):
         cfg = PoolConfig(k_max=k_max, flags=flags, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
-                         cuda_stream=stream or 0, tol_rel=tol_rel, orth_every=orth_every, orth_tol=orth_tol)
+                         cuda_stream=stream or 0, tol_rel=tol_rel, orth_every=orth_every, orth_tol=orth_tol,
+                         rank_every=rank_every, tau_evr=tau_evr)
         h = C.c_void_p()
         st = lib().isvd_pool_create(C.byref(cfg), C.byref(h))
         if st:
@@ -400,6 +412,36 @@ class Pool:
         cnt = (C.c_int64 * n)()
         self._check(lib().isvd_pool_profile_read(self._p, ms, cnt, n), "isvd_pool_profile_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.POOL_KCLASSES)}
+
+    def poll(self, cap=1 << 16):
+        """Completion records of finished ops not returned before (pool made with POOL_COMPLETIONS),
+        as a NumPy structured array (fields of isvd_completion)."""
+        buf = (Completion * max(cap, 1))()
+        n = C.c_int64()
+        self._check(lib().isvd_pool_poll(self._p, buf, cap, C.byref(n)), "isvd_pool_poll")
+        dt = np.dtype([("seq", np.int64), ("stream", np.int32), ("kind", np.int32), ("status", np.int32),
+                       ("r", np.int32), ("rho", np.float64), ("sigma_max", np.float64), ("done_ns", np.uint64)])
+        return np.frombuffer(bytes(buf)[:n.value * C.sizeof(Completion)], dtype=dt).copy()
+
+    @property
+    def slots(self):
+        return int(lib().isvd_pool_slots(self._p))
+
+    def gather_sigma(self, ld, out=None):
+        """Singular values of every slot, (slots x ld) doubles zero-padded; ``out`` may be a CUDA
+        tensor or a (pinned) host array, filled asynchronously on the pool's stream."""
+        if out is None:
+            out = np.zeros((self.slots, ld), np.float64)
+        ptr, dev = _ptr(out)
+        self._check(lib().isvd_pool_gather_sigma(self._p, int(ld), ptr, dev), "isvd_pool_gather_sigma")
+        return out
+
+    def host_profile(self):
+        """{phase: host microseconds} of the submits since profile(True), and their count."""
+        us = (C.c_double * 4)()
+        n = C.c_int64()
+        self._check(lib().isvd_pool_host_profile(self._p, us, 4, C.byref(n)), "isvd_pool_host_profile")
+        return dict(zip(("validate", "order", "stage", "enqueue"), us)), n.value
 
     def stream(self, sid):
         h = lib().isvd_pool_stream(self._p, int(sid))

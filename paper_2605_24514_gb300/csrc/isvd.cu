@@ -5,9 +5,11 @@
 // handle's CUDA stream with no host round trip; the host synchronises only for metrics, policy
 // checks and explicit reads.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -42,6 +44,7 @@ struct isvd_ctx {
   double orth_tol = 1e-12;
   int64_t orth_every = 0, since_orth = 0;
   int orth_on_device = 0;  // the batched path's monitor (DevState orth_u/v, reorths) runs this stream
+  int64_t since_rank = 0;  // the batched path's adaptive-rank cadence
   void* Uref = nullptr;
   int64_t m_ref = 0, uref_cap = 0;
   int r_ref = 0;
@@ -755,8 +758,14 @@ isvd_status store_ref(isvd_ctx* h, int r) {
 
 template <typename T>
 isvd_status do_refresh(isvd_ctx* h, int store) {
-  const int kr = (int)std::min<int64_t>(h->k_host, std::min(h->m, h->n));
   isvd_status s;
+  if (h->orth_on_device) {
+    // A pool stream's working rank may have been grown on the device by the batched rank rule.
+    DevState ds;
+    if ((s = read_state(h, &ds))) return s;
+    h->k_host = ds.k;
+  }
+  const int kr = (int)std::min<int64_t>(h->k_host, std::min(h->m, h->n));
   if (h->opt_t == h->t && h->opt_rank == kr && h->Uopt && h->Vopt) {
     // The policy check at this same t already computed TruncatedSVD(A_t, kr) for its metrics.
     CK(h, cudaMemcpyAsync(h->U, h->Uopt, (size_t)h->m * h->ld * h->es, cudaMemcpyDeviceToDevice, h->stream));
@@ -1361,10 +1370,41 @@ struct isvd_pool_ctx {
   int flags = 0;
   int64_t orth_every = 256;  // <= 0: no monitor
   double orth_tol = 1e-5;
-  PoolReorthOp* reorth_pinned = nullptr;  // per submit: the monitor's stream list of every tick
-  PoolReorthOp* reorth_dev = nullptr;
+  PoolReorthOp* reorth_dev = nullptr;  // per submit: the monitor's stream list of every tick
+  // Completion records (ISVD_POOL_COMPLETIONS): written per tick into comp_dev, copied per submit
+  // into a pinned batch; isvd_pool_poll hands out batches whose event has completed.
+  int64_t seq_next = 0;
+  PoolCompletion* comp_dev = nullptr;
+  int64_t comp_cap = 0;
+  struct CompBatch {
+    PoolCompletion* host = nullptr;
+    int64_t cap = 0, count = 0, taken = 0;
+    cudaEvent_t ev = nullptr;
+  };
+  std::deque<CompBatch> comp_q;
+  std::vector<CompBatch> comp_free;
+  // Per-slot device tables of the streams' sigma and state pointers (sigma gather); released
+  // slots point at zeroed stand-ins.
+  const double** tab_sig = nullptr;
+  const DevState** tab_st = nullptr;
+  int64_t tab_cap = 0;
+  double* zero_sig = nullptr;
+  DevState* zero_st = nullptr;
+  double* gather_dev = nullptr;
+  int64_t gather_cap = 0;
   int64_t reorth_cap = 0;
   int64_t reorth_runs = 0;
+  // Streams whose monitor is due; checked together once a full wave of them has gathered (or one
+  // of them is overdue by a whole cadence), so that the check costs one short launch per wave.
+  std::vector<int32_t> reorth_pending;
+  // Adaptive rank (rank_every > 0): streams due after each tick of a submit.
+  int64_t rank_every = 0;
+  double tau_evr = 0.9;
+  std::vector<PoolRankOp> v_rank;
+  std::vector<int64_t> v_rank_start;
+  PoolRankOp* rank_dev = nullptr;
+  int64_t rank_cap = 0;
+  std::vector<int64_t> reorth_due_t;  // per slot: pool tick at which the stream became due (-1: none)
   cudaStream_t stream = nullptr;
   int64_t budget = 0, used = 0, max_streams = 0;
   double tol_rel = 3e-6;
@@ -1373,19 +1413,29 @@ struct isvd_pool_ctx {
   std::vector<int64_t> bytes;
   PoolOp* ops_dev = nullptr;
   int64_t ops_cap = 0;
-  PoolOp* ops_pinned = nullptr;
-  int64_t pinned_cap = 0;
+  // Host staging of a submit's descriptors, double-buffered: a submit fills one slot while the
+  // previous submit's copies from the other may still be pending, so the host waits only when it
+  // runs two submits ahead of the device.
+  struct Stage {
+    PoolOp* ops = nullptr;
+    int* chunks = nullptr;
+    int64_t cap = 0;
+    PoolReorthOp* reorth = nullptr;
+    int64_t reorth_cap = 0;
+    PoolRankOp* rank = nullptr;
+    int64_t rank_cap = 0;
+    cudaEvent_t copied = nullptr;
+  } stage[2];
+  int stage_cur = 0;
   void* payload = nullptr;
   int64_t payload_cap = 0;
-  cudaEvent_t copied = nullptr;
   int* retry_list = nullptr;  // per-tick list of warp-path updates handed to the CTA kernel
   int64_t retry_cap = 0;
   int* retry_n = nullptr;     // one counter per tick of a submit
   int64_t retry_n_cap = 0;
   void* rot_scratch = nullptr;  // per-update records from the warp kernel to the rotation kernel
   int64_t rot_cap = 0;          // updates
-  int* chunks_pinned = nullptr;  // first rotation block of each update (per bucket run)
-  int* chunks_dev = nullptr;
+  int* chunks_dev = nullptr;  // first rotation block of each update (per bucket run)
   int64_t chunks_cap = 0;
   int* block_op = nullptr;  // rotation block -> update, written by the warp kernels
   int64_t block_op_cap = 0;
@@ -1401,7 +1451,17 @@ struct isvd_pool_ctx {
   std::vector<uint8_t> s_bucket;
   uint32_t gen = 0;
   std::vector<int32_t> touched;
+  // Reused host scratch of a submit (no allocation per call once grown).
+  std::vector<int32_t> v_tick_of;
+  std::vector<int64_t> v_order, v_tick_start, v_tmp, v_fill, v_run_boff, v_reorth_start;
+  std::vector<uint8_t> v_key;
+  std::vector<char> v_fused;
+  std::vector<int> v_run_blocks;
+  std::vector<PoolReorthOp> v_reorth;
   int64_t launches = 0, ticks = 0, fused_ops = 0, fallback_ops = 0, warp_ops = 0;
+  // Host time of submits by phase (validate, order, stage, enqueue), while profiling.
+  double host_us[4] = {0, 0, 0, 0};
+  int64_t host_submits = 0;
   // Optional per-class launch timing (isvd_pool_profile).
   int prof = 0;
   std::vector<cudaEvent_t> prof_ev;
@@ -1456,7 +1516,8 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
                              const int* chunks, int* block_op) {
   void* scr = static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
-  cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op);
+  cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op,
+                                   pool_rot_rows(KB, !(p->flags & ISVD_POOL_SIMT_ROTATIONS)));
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1487,6 +1548,39 @@ isvd_status pool_launch_retry(isvd_pool_ctx* p, const PoolOp* ops, int count, in
   return ISVD_OK;
 }
 
+// Points slot id of the sigma-gather tables at (sig, st), growing the tables as needed.
+isvd_status pool_set_slot(isvd_pool_ctx* p, int64_t id, const double* sig, const DevState* st) {
+  if (id >= p->tab_cap) {
+    const int64_t cap = std::max<int64_t>(id + 1, 2 * p->tab_cap);
+    const double** ts = nullptr;
+    const DevState** tt = nullptr;
+    if (cudaMalloc((void**)&ts, sizeof(void*) * cap) != cudaSuccess ||
+        cudaMalloc((void**)&tt, sizeof(void*) * cap) != cudaSuccess) {
+      if (ts) cudaFree(ts);
+      return pool_fail(p, ISVD_ENOMEM, "pool slot tables");
+    }
+    std::vector<const void*> zs(cap, p->zero_sig), zt(cap, p->zero_st);
+    cudaStreamSynchronize(p->stream);
+    if (p->tab_cap > 0) {
+      cudaMemcpy(zs.data(), p->tab_sig, sizeof(void*) * p->tab_cap, cudaMemcpyDeviceToHost);
+      cudaMemcpy(zt.data(), p->tab_st, sizeof(void*) * p->tab_cap, cudaMemcpyDeviceToHost);
+    }
+    cudaMemcpy(ts, zs.data(), sizeof(void*) * cap, cudaMemcpyHostToDevice);
+    cudaMemcpy(tt, zt.data(), sizeof(void*) * cap, cudaMemcpyHostToDevice);
+    if (p->tab_sig) cudaFree(p->tab_sig);
+    if (p->tab_st) cudaFree(p->tab_st);
+    p->tab_sig = ts;
+    p->tab_st = tt;
+    p->tab_cap = cap;
+  }
+  // Stream-ordered, so gathers queued earlier still see the old entry.
+  if (cudaMemcpyAsync(p->tab_sig + id, &sig, sizeof(void*), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(p->tab_st + id, &st, sizeof(void*), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool slot tables");
+  return ISVD_OK;
+}
+
 int64_t stream_footprint(int64_t row_cap, int64_t col_cap, int ld) {
   // U, V, U_ref and A in FP32 plus the handle's fixed workspace.
   const int64_t fixed = (int64_t)6 * (kKmaxLimit + 1) * (kKmaxLimit + 1) * 8 + (int64_t)kMaxProjBlocks * kPartStride * 8 +
@@ -1501,7 +1595,7 @@ extern "C" {
 isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (!cfg || !out) return ISVD_EINVAL;
   *out = nullptr;
-  if (cfg->k_max < 1 || cfg->k_max > 64) return ISVD_EINVAL;
+  if (cfg->k_max < 1 || cfg->k_max > kKmaxLimit) return ISVD_EINVAL;
   isvd_pool_ctx* p = new isvd_pool_ctx();
   p->kmax = cfg->k_max;
   p->kb = kb_bucket(cfg->k_max);
@@ -1512,6 +1606,8 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->flags = cfg->flags;
   p->orth_every = cfg->orth_every == 0 ? 256 : cfg->orth_every;
   p->orth_tol = cfg->orth_tol > 0 ? cfg->orth_tol : 1e-5;
+  p->rank_every = cfg->rank_every > 0 ? cfg->rank_every : 0;
+  p->tau_evr = cfg->tau_evr;
   p->cfg.prec = ISVD_FP32;
   p->cfg.k_max = p->kmax;
   p->cfg.tol_rel = p->tol_rel;
@@ -1535,7 +1631,12 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_w[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_r[i], cudaEventDisableTiming);
   }
-  if (e != cudaSuccess || cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming) != cudaSuccess) {
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->stage[i].copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->zero_sig, 8 * (kKmaxLimit + 2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->zero_st, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMemset(p->zero_sig, 0, 8 * (kKmaxLimit + 2));
+  if (e == cudaSuccess) e = cudaMemset(p->zero_st, 0, sizeof(DevState));
+  if (e != cudaSuccess) {
     delete p;
     return ISVD_ECUDA;
   }
@@ -1561,12 +1662,30 @@ void isvd_pool_destroy(isvd_pool_t p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->chunks_dev) cudaFree(p->chunks_dev);
-  if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
   if (p->reorth_dev) cudaFree(p->reorth_dev);
-  if (p->reorth_pinned) cudaFreeHost(p->reorth_pinned);
-  if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
+  if (p->comp_dev) cudaFree(p->comp_dev);
+  if (p->rank_dev) cudaFree(p->rank_dev);
+  for (auto& b : p->comp_q) {
+    if (b.host) cudaFreeHost(b.host);
+    if (b.ev) cudaEventDestroy(b.ev);
+  }
+  for (auto& b : p->comp_free) {
+    if (b.host) cudaFreeHost(b.host);
+    if (b.ev) cudaEventDestroy(b.ev);
+  }
+  if (p->tab_sig) cudaFree(p->tab_sig);
+  if (p->tab_st) cudaFree(p->tab_st);
+  if (p->zero_sig) cudaFree(p->zero_sig);
+  if (p->zero_st) cudaFree(p->zero_st);
+  if (p->gather_dev) cudaFree(p->gather_dev);
+  for (auto& sg : p->stage) {
+    if (sg.ops) cudaFreeHost(sg.ops);
+    if (sg.chunks) cudaFreeHost(sg.chunks);
+    if (sg.reorth) cudaFreeHost(sg.reorth);
+    if (sg.rank) cudaFreeHost(sg.rank);
+    if (sg.copied) cudaEventDestroy(sg.copied);
+  }
   if (p->payload) cudaFree(p->payload);
-  if (p->copied) cudaEventDestroy(p->copied);
   delete p;
 }
 
@@ -1610,6 +1729,7 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   // made together are not all checked in the same tick.
   h->orth_on_device = 1;
   h->since_orth = p->orth_every > 0 ? ((int64_t)id * 37) % p->orth_every : 0;
+  if ((s = pool_set_slot(p, id, h->sig, h->st))) return s;
   if (p->s_gen.size() < p->streams.size()) {
     const size_t ns = p->streams.size();
     p->s_m.resize(ns);
@@ -1630,6 +1750,11 @@ isvd_status isvd_pool_release(isvd_pool_t p, int32_t sid) {
   cudaStreamSynchronize(p->stream);
   isvd_destroy(p->streams[sid]);
   p->streams[sid] = nullptr;
+  pool_set_slot(p, sid, p->zero_sig, p->zero_st);
+  if (sid < (int32_t)p->reorth_due_t.size() && p->reorth_due_t[sid] >= 0) {
+    p->reorth_due_t[sid] = -1;
+    p->reorth_pending.erase(std::find(p->reorth_pending.begin(), p->reorth_pending.end(), sid));
+  }
   p->used -= p->bytes[sid];
   p->bytes[sid] = 0;
   return ISVD_OK;
@@ -1651,7 +1776,16 @@ isvd_status isvd_pool_profile(isvd_pool_t p, int enable) {
   if (enable) {
     p->prof_used = 0;
     p->prof_spans.clear();
+    for (double& v : p->host_us) v = 0.0;
+    p->host_submits = 0;
   }
+  return ISVD_OK;
+}
+
+isvd_status isvd_pool_host_profile(isvd_pool_t p, double* us_out, int n, int64_t* submits) {
+  if (!p || !us_out || n < 0 || n > 4) return ISVD_EINVAL;
+  for (int i = 0; i < n; ++i) us_out[i] = p->host_us[i];
+  if (submits) *submits = p->host_submits;
   return ISVD_OK;
 }
 
@@ -1679,6 +1813,8 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   if (!p || (nops > 0 && !ops)) return ISVD_EINVAL;
   if (nops == 0) return ISVD_OK;
   const size_t es = 4;
+  using clk = std::chrono::steady_clock;
+  const auto h0 = clk::now();
   // Validate every op against the shapes it will see (per-stream order), before any work. Only
   // the streams named by the ops are read (their shapes into the pool's per-stream scratch).
   if (++p->gen == 0) {
@@ -1690,7 +1826,8 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   std::vector<int64_t>& nn = p->s_n;
   std::vector<int32_t>& seen = p->s_seen;
   p->touched.clear();
-  std::vector<int32_t> tick_of(nops);
+  std::vector<int32_t>& tick_of = p->v_tick_of;
+  tick_of.resize(nops);
   int32_t nticks = 0;
   for (int64_t e = 0; e < nops; ++e) {
     const isvd_op& o = ops[e];
@@ -1740,38 +1877,54 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       return pool_fail(p, ISVD_ECUDA, "pool payload copy");
     pay = (const float*)p->payload;
   }
+  const auto h1 = clk::now();
   // Order ops by tick (stable), build descriptors, then one descriptor copy for all ticks.
-  std::vector<int64_t> order(nops), tick_start(nticks + 1, 0);
+  std::vector<int64_t>& order = p->v_order;
+  std::vector<int64_t>& tick_start = p->v_tick_start;
+  order.resize(nops);
+  tick_start.assign(nticks + 1, 0);
   for (int64_t e = 0; e < nops; ++e) tick_start[tick_of[e] + 1]++;
   for (int32_t t = 0; t < nticks; ++t) tick_start[t + 1] += tick_start[t];
   {
-    std::vector<int64_t> fill(tick_start.begin(), tick_start.end() - 1);
+    std::vector<int64_t>& fill = p->v_fill;
+    fill.assign(tick_start.begin(), tick_start.end() - 1);
     for (int64_t e = 0; e < nops; ++e) order[fill[tick_of[e]]++] = e;
     // Within a tick: first the appends of rank capacity <= 32 (one warp-per-update launch, the
     // widest buckets first so the longest updates start first), then the CTA kernel's updates
     // grouped by rank bucket (one launch per bucket, the narrowest instance that fits).
-    // Counting sort (stable) on a small key: 0-2 warp buckets 32/16/8, 3-6 CTA buckets 8-64.
-    std::vector<uint8_t> key(nops);
+    // Counting sort (stable) on a small key: 0-2 warp buckets 32/16/8, 3-6 CTA buckets 8-64, 7
+    // bucket 128 (single-stream kernels).
+    std::vector<uint8_t>& key = p->v_key;
+    key.resize(nops);
     for (int64_t e = 0; e < nops; ++e) {
       const int b = p->s_bucket[ops[e].stream];
-      const int lb = b == 8 ? 0 : b == 16 ? 1 : b == 32 ? 2 : 3;
+      const int lb = b == 8 ? 0 : b == 16 ? 1 : b == 32 ? 2 : b == 64 ? 3 : 4;
       key[e] = (uint8_t)((ops[e].kind != kEntry && b <= kWarpKB) ? 2 - lb : 3 + lb);
     }
-    std::vector<int64_t> tmp(nops);
+    std::vector<int64_t>& tmp = p->v_tmp;
+    tmp.resize(nops);
     for (int32_t t = 0; t < nticks; ++t) {
-      int64_t cnt[8] = {};
+      int64_t cnt[9] = {};
       for (int64_t z = tick_start[t]; z < tick_start[t + 1]; ++z) cnt[key[order[z]] + 1]++;
-      for (int k = 1; k < 8; ++k) cnt[k] += cnt[k - 1];
+      for (int k = 1; k < 9; ++k) cnt[k] += cnt[k - 1];
       for (int64_t z = tick_start[t]; z < tick_start[t + 1]; ++z) tmp[tick_start[t] + cnt[key[order[z]]]++] = order[z];
       std::copy(tmp.begin() + tick_start[t], tmp.begin() + tick_start[t + 1], order.begin() + tick_start[t]);
     }
   }
-  if (nops > p->pinned_cap) {
-    cudaEventSynchronize(p->copied);
-    if (p->ops_pinned) cudaFreeHost(p->ops_pinned);
-    p->pinned_cap = std::max<int64_t>(nops, 2 * p->pinned_cap);
-    if (cudaMallocHost((void**)&p->ops_pinned, sizeof(PoolOp) * (size_t)p->pinned_cap) != cudaSuccess) {
-      p->pinned_cap = 0;
+  const auto h2 = clk::now();
+  // This submit's staging slot: its previous user's copies (two submits ago) must have finished.
+  isvd_pool_ctx::Stage& sg = p->stage[p->stage_cur];
+  p->stage_cur ^= 1;
+  cudaEventSynchronize(sg.copied);
+  if (nops > sg.cap) {
+    if (sg.ops) cudaFreeHost(sg.ops);
+    if (sg.chunks) cudaFreeHost(sg.chunks);
+    sg.ops = nullptr;
+    sg.chunks = nullptr;
+    sg.cap = std::max<int64_t>(nops, 2 * sg.cap);
+    if (cudaMallocHost((void**)&sg.ops, sizeof(PoolOp) * (size_t)sg.cap) != cudaSuccess ||
+        cudaMallocHost((void**)&sg.chunks, sizeof(int) * (size_t)sg.cap) != cudaSuccess) {
+      sg.cap = 0;
       return pool_fail(p, ISVD_ENOMEM, "pool pinned descriptors");
     }
   }
@@ -1820,17 +1973,13 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   if (nops > p->chunks_cap) {
     cudaStreamSynchronize(p->stream);
     if (p->chunks_dev) cudaFree(p->chunks_dev);
-    if (p->chunks_pinned) cudaFreeHost(p->chunks_pinned);
     p->chunks_dev = nullptr;
-    p->chunks_pinned = nullptr;
     p->chunks_cap = std::max<int64_t>(nops, 2 * p->chunks_cap);
-    if (cudaMalloc((void**)&p->chunks_dev, sizeof(int) * (size_t)p->chunks_cap) != cudaSuccess ||
-        cudaMallocHost((void**)&p->chunks_pinned, sizeof(int) * (size_t)p->chunks_cap) != cudaSuccess) {
+    if (cudaMalloc((void**)&p->chunks_dev, sizeof(int) * (size_t)p->chunks_cap) != cudaSuccess) {
       p->chunks_cap = 0;
       return pool_fail(p, ISVD_ENOMEM, "pool rotation tables");
     }
   }
-  cudaEventSynchronize(p->copied);  // the previous submit's descriptor copy has finished
   isvd_status s;
   // Grow every named stream to its final shape for this submit BEFORE building descriptors, so
   // that no reallocation can invalidate a descriptor or copy data ahead of queued work.
@@ -1839,20 +1988,30 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     if ((s = ensure_rows(h, mm[sid] + 1))) return s;
     if ((s = ensure_cols(h, nn[sid] + 1))) return s;
   }
-  std::vector<char> fused(nops, 0);
+  std::vector<char>& fused = p->v_fused;
+  fused.assign(nops, 0);
   // Streams whose monitor is due, per tick (checked after that tick's updates).
-  std::vector<PoolReorthOp> reorth;
-  std::vector<int64_t> reorth_start(nticks + 1, 0);
+  std::vector<PoolReorthOp>& reorth = p->v_reorth;
+  std::vector<int64_t>& reorth_start = p->v_reorth_start;
+  reorth.clear();
+  reorth_start.assign(nticks + 1, 0);
+  if ((int64_t)p->reorth_due_t.size() < (int64_t)p->streams.size()) p->reorth_due_t.resize(p->streams.size(), -1);
+  std::vector<PoolRankOp>& rank = p->v_rank;
+  std::vector<int64_t>& rank_start = p->v_rank_start;
+  rank.clear();
+  rank_start.assign(nticks + 1, 0);
   for (int32_t t = 0; t < nticks; ++t) {
     reorth_start[t] = (int64_t)reorth.size();
+    rank_start[t] = (int64_t)rank.size();
     for (int64_t q = tick_start[t]; q < tick_start[t + 1]; ++q) {
       const int64_t e = order[q];
       const isvd_op& o = ops[e];
       isvd_ctx* h = p->streams[o.stream];
       const int64_t prow = o.kind == kRow ? h->n : h->m;
-      if (o.kind != kEntry && p->s_bucket[o.stream] <= kWarpKB) fused[q] = 2;  // warp per update
-      else fused[q] = (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
-      PoolOp& d = p->ops_pinned[q];
+      const int bk = p->s_bucket[o.stream];
+      if (o.kind != kEntry && bk <= kWarpKB) fused[q] = 2;  // warp per update
+      else fused[q] = bk <= 64 && (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
+      PoolOp& d = sg.ops[q];
       d.U = (float*)h->U;
       d.V = (float*)h->V;
       d.A = (float*)h->A;
@@ -1868,33 +2027,83 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       d.tol_rel = h->tol_rel;
       d.ld = h->ld;
       d.kind = o.kind;
+      d.sid = o.stream;
+      d.pad = 0;
+      d.seq = p->seq_next + e;
       if (o.kind == kRow) h->m += 1;
       else if (o.kind == kCol) h->n += 1;
       h->t += 1;
-      if (p->orth_every > 0 && ++h->since_orth >= p->orth_every) {
-        h->since_orth = 0;
-        reorth.push_back(PoolReorthOp{(float*)h->U, (float*)h->V, h->st, h->m, h->n, h->ld, 0});
+      if (p->rank_every > 0 && ++h->since_rank >= p->rank_every) {
+        h->since_rank = 0;
+        rank.push_back(PoolRankOp{h->st, h->sig, std::min<int32_t>(p->s_bucket[o.stream], p->kmax), 0});
       }
+      // Due at half the cadence; checked within another half (sooner once a wave has gathered).
+      if (p->orth_every > 0 && ++h->since_orth >= (p->orth_every + 1) / 2 && p->reorth_due_t[o.stream] < 0) {
+        p->reorth_due_t[o.stream] = p->ticks + t;
+        p->reorth_pending.push_back(o.stream);
+      }
+    }
+    // After this tick: check the pending streams once they fill a wave of CTAs, or when the oldest
+    // has waited half a cadence, so that no stream goes longer than orth_every updates unchecked.
+    const int64_t now = p->ticks + t;
+    const bool full = (int64_t)p->reorth_pending.size() >= p->num_sms;
+    const bool overdue =
+        !p->reorth_pending.empty() && now - p->reorth_due_t[p->reorth_pending.front()] >= p->orth_every / 2;
+    if (full || overdue) {
+      for (const int32_t sid : p->reorth_pending) {
+        isvd_ctx* h = p->streams[sid];
+        reorth.push_back(PoolReorthOp{(float*)h->U, (float*)h->V, h->st, h->m, h->n, h->ld, 0});
+        h->since_orth = 0;
+        p->reorth_due_t[sid] = -1;
+      }
+      p->reorth_pending.clear();
     }
   }
   reorth_start[nticks] = (int64_t)reorth.size();
+  rank_start[nticks] = (int64_t)rank.size();
+  if ((int64_t)rank.size() > p->rank_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->rank_dev) cudaFree(p->rank_dev);
+    p->rank_dev = nullptr;
+    p->rank_cap = std::max<int64_t>((int64_t)rank.size(), 2 * p->rank_cap);
+    if (cudaMalloc((void**)&p->rank_dev, sizeof(PoolRankOp) * (size_t)p->rank_cap) != cudaSuccess) {
+      p->rank_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool rank list");
+    }
+  }
+  if ((int64_t)rank.size() > sg.rank_cap) {
+    if (sg.rank) cudaFreeHost(sg.rank);
+    sg.rank = nullptr;
+    sg.rank_cap = std::max<int64_t>((int64_t)rank.size(), 2 * sg.rank_cap);
+    if (cudaMallocHost((void**)&sg.rank, sizeof(PoolRankOp) * (size_t)sg.rank_cap) != cudaSuccess) {
+      sg.rank_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool rank list");
+    }
+  }
   if ((int64_t)reorth.size() > p->reorth_cap) {
     cudaStreamSynchronize(p->stream);
     if (p->reorth_dev) cudaFree(p->reorth_dev);
-    if (p->reorth_pinned) cudaFreeHost(p->reorth_pinned);
     p->reorth_dev = nullptr;
-    p->reorth_pinned = nullptr;
     p->reorth_cap = std::max<int64_t>((int64_t)reorth.size(), 2 * p->reorth_cap);
-    if (cudaMalloc((void**)&p->reorth_dev, sizeof(PoolReorthOp) * (size_t)p->reorth_cap) != cudaSuccess ||
-        cudaMallocHost((void**)&p->reorth_pinned, sizeof(PoolReorthOp) * (size_t)p->reorth_cap) != cudaSuccess) {
+    if (cudaMalloc((void**)&p->reorth_dev, sizeof(PoolReorthOp) * (size_t)p->reorth_cap) != cudaSuccess) {
       p->reorth_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool monitor list");
+    }
+  }
+  if ((int64_t)reorth.size() > sg.reorth_cap) {
+    if (sg.reorth) cudaFreeHost(sg.reorth);
+    sg.reorth = nullptr;
+    sg.reorth_cap = std::max<int64_t>((int64_t)reorth.size(), 2 * sg.reorth_cap);
+    if (cudaMallocHost((void**)&sg.reorth, sizeof(PoolReorthOp) * (size_t)sg.reorth_cap) != cudaSuccess) {
+      sg.reorth_cap = 0;
       return pool_fail(p, ISVD_ENOMEM, "pool monitor list");
     }
   }
   auto bucket_at = [&](int64_t z) { return (int)p->s_bucket[ops[order[z]].stream]; };
   // Rotation block tables of the warp-kernel runs (one run per tick and rank bucket):
   // chunks[q] = first block of update q within its run; run_blocks[first q of a run] = total.
-  std::vector<int> run_blocks(nops, 0);
+  std::vector<int>& run_blocks = p->v_run_blocks;
+  run_blocks.assign(nops, 0);
   for (int32_t t = 0; t < nticks; ++t) {
     int64_t q = tick_start[t];
     while (q < tick_start[t + 1]) {
@@ -1905,10 +2114,11 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       int64_t b1 = q;
       int tot = 0;
       while (b1 < tick_start[t + 1] && fused[b1] == 2 && bucket_at(b1) == bucket_at(q)) {
-        const PoolOp& d = p->ops_pinned[b1];
+        const PoolOp& d = sg.ops[b1];
         const int64_t nP = d.kind == kRow ? d.n : d.m, nQ = d.kind == kRow ? d.m : d.n;
-        p->chunks_pinned[b1] = tot;
-        tot += (int)((nP + kPoolRotRows - 1) / kPoolRotRows + (nQ + kPoolRotRows - 1) / kPoolRotRows);
+        const int rr = pool_rot_rows(bucket_at(q), !(p->flags & ISVD_POOL_SIMT_ROTATIONS));
+        sg.chunks[b1] = tot;
+        tot += (int)((nP + rr - 1) / rr + (nQ + rr - 1) / rr);
         ++b1;
       }
       run_blocks[q] = tot;
@@ -1916,13 +2126,25 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     }
   }
   // Each run's block -> update table sits at its own offset (runs of one tick run concurrently).
-  std::vector<int64_t> run_boff(nops, 0);
+  std::vector<int64_t>& run_boff = p->v_run_boff;
+  run_boff.assign(nops, 0);
   int64_t total_blocks = 0;
   for (int64_t q = 0; q < nops; ++q)
     if (run_blocks[q]) {
       run_boff[q] = total_blocks;
       total_blocks += run_blocks[q];
     }
+  const bool completions = (p->flags & ISVD_POOL_COMPLETIONS) != 0;
+  if (completions && nops > p->comp_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->comp_dev) cudaFree(p->comp_dev);
+    p->comp_dev = nullptr;
+    p->comp_cap = std::max<int64_t>(nops, 2 * p->comp_cap);
+    if (cudaMalloc((void**)&p->comp_dev, sizeof(PoolCompletion) * (size_t)p->comp_cap) != cudaSuccess) {
+      p->comp_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool completion records");
+    }
+  }
   if (total_blocks > p->block_op_cap) {
     cudaStreamSynchronize(p->stream);
     if (p->block_op) cudaFree(p->block_op);
@@ -1933,18 +2155,25 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       return pool_fail(p, ISVD_ENOMEM, "pool rotation block table");
     }
   }
-  if (cudaMemcpyAsync(p->ops_dev, p->ops_pinned, sizeof(PoolOp) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
+  const auto h3 = clk::now();
+  if (cudaMemcpyAsync(p->ops_dev, sg.ops, sizeof(PoolOp) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(p->chunks_dev, p->chunks_pinned, sizeof(int) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
+      cudaMemcpyAsync(p->chunks_dev, sg.chunks, sizeof(int) * (size_t)nops, cudaMemcpyHostToDevice, p->stream) !=
           cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool descriptor copy");
   if (!reorth.empty()) {
-    std::copy(reorth.begin(), reorth.end(), p->reorth_pinned);
-    if (cudaMemcpyAsync(p->reorth_dev, p->reorth_pinned, sizeof(PoolReorthOp) * reorth.size(), cudaMemcpyHostToDevice,
+    std::copy(reorth.begin(), reorth.end(), sg.reorth);
+    if (cudaMemcpyAsync(p->reorth_dev, sg.reorth, sizeof(PoolReorthOp) * reorth.size(), cudaMemcpyHostToDevice,
                         p->stream) != cudaSuccess)
       return pool_fail(p, ISVD_ECUDA, "pool monitor list copy");
   }
-  cudaEventRecord(p->copied, p->stream);
+  if (!rank.empty()) {
+    std::copy(rank.begin(), rank.end(), sg.rank);
+    if (cudaMemcpyAsync(p->rank_dev, sg.rank, sizeof(PoolRankOp) * rank.size(), cudaMemcpyHostToDevice,
+                        p->stream) != cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool rank list copy");
+  }
+  cudaEventRecord(sg.copied, p->stream);
   if (cudaMemsetAsync(p->retry_n, 0, sizeof(int) * (size_t)nticks, p->stream) != cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool retry counters");
   for (int32_t t = 0; t < nticks; ++t) {
@@ -2004,13 +2233,13 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
         p->fused_ops += cnt;
       } else {
         for (int64_t z = q; z < q2; ++z) {
-          const PoolOp& d = p->ops_pinned[z];
+          const PoolOp& d = sg.ops[z];
           isvd_ctx* h = p->streams[ops[order[z]].stream];
           // Replay the shape the op saw, run the single-stream path, restore the advanced shape.
           const int64_t m_after = h->m, n_after = h->n;
           h->m = d.m;
           h->n = d.n;
-          s = do_append<float>(h, d.kind, d.x);
+          s = d.kind == kEntry ? do_entry<float>(h, d.i, d.j, d.delta) : do_append<float>(h, d.kind, d.x);
           h->m = m_after;
           h->n = n_after;
           if (s) return s;
@@ -2026,7 +2255,58 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       p->launches++;
       p->reorth_runs += nre;
     }
+    const int64_t nrk = rank_start[t + 1] - rank_start[t];
+    if (nrk > 0) {
+      const cudaError_t e = pool_rank_launch((int)nrk, p->stream, p->rank_dev + rank_start[t], p->tau_evr);
+      if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rank launch: ") + cudaGetErrorString(e));
+      p->launches++;
+    }
+    if (completions) {
+      const int64_t cnt = tick_start[t + 1] - tick_start[t];
+      const cudaError_t e = pool_complete_launch((int)cnt, p->stream, p->ops_dev + tick_start[t], p->comp_dev + tick_start[t]);
+      if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool completion launch: ") + cudaGetErrorString(e));
+      p->launches++;
+    }
     p->ticks++;
+  }
+  if (completions) {
+    isvd_pool_ctx::CompBatch b;
+    for (size_t i = 0; i < p->comp_free.size(); ++i)
+      if (p->comp_free[i].cap >= nops) {
+        b = p->comp_free[i];
+        p->comp_free.erase(p->comp_free.begin() + (int64_t)i);
+        break;
+      }
+    if (!b.host) {
+      b.cap = std::max<int64_t>(nops, 4096);
+      if (cudaMallocHost((void**)&b.host, sizeof(PoolCompletion) * (size_t)b.cap) != cudaSuccess)
+        return pool_fail(p, ISVD_ENOMEM, "pool completion batch");
+      if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(b.host);
+        return pool_fail(p, ISVD_ECUDA, "pool completion event");
+      }
+    }
+    b.count = nops;
+    b.taken = 0;
+    if (cudaMemcpyAsync(b.host, p->comp_dev, sizeof(PoolCompletion) * (size_t)nops, cudaMemcpyDeviceToHost,
+                        p->stream) != cudaSuccess ||
+        cudaEventRecord(b.ev, p->stream) != cudaSuccess) {
+      p->comp_free.push_back(b);
+      return pool_fail(p, ISVD_ECUDA, "pool completion copy");
+    }
+    p->comp_q.push_back(b);
+  }
+  p->seq_next += nops;
+  if (p->prof) {
+    const auto h4 = clk::now();
+    const auto us = [](clk::time_point a, clk::time_point b) {
+      return std::chrono::duration<double, std::micro>(b - a).count();
+    };
+    p->host_us[0] += us(h0, h1);
+    p->host_us[1] += us(h1, h2);
+    p->host_us[2] += us(h2, h3);
+    p->host_us[3] += us(h3, h4);
+    p->host_submits++;
   }
   return ISVD_OK;
 }
@@ -2040,6 +2320,57 @@ isvd_status isvd_pool_sync(isvd_pool_t p) {
     isvd_status s = read_state(h, &ds);
     if (s) return s;
   }
+  return ISVD_OK;
+}
+
+isvd_status isvd_pool_poll(isvd_pool_t p, isvd_completion* out, int64_t cap, int64_t* nout) {
+  static_assert(sizeof(isvd_completion) == sizeof(PoolCompletion), "completion record layout");
+  if (!p || !nout || cap < 0 || (cap > 0 && !out)) return ISVD_EINVAL;
+  *nout = 0;
+  if (!(p->flags & ISVD_POOL_COMPLETIONS)) return pool_fail(p, ISVD_EINVAL, "pool created without completions");
+  while (!p->comp_q.empty() && *nout < cap) {
+    isvd_pool_ctx::CompBatch& b = p->comp_q.front();
+    const cudaError_t q = cudaEventQuery(b.ev);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool poll: ") + cudaGetErrorString(q));
+    const int64_t take = std::min(cap - *nout, b.count - b.taken);
+    std::memcpy(out + *nout, b.host + b.taken, sizeof(PoolCompletion) * (size_t)take);
+    b.taken += take;
+    *nout += take;
+    if (b.taken == b.count) {
+      p->comp_free.push_back(b);
+      p->comp_q.pop_front();
+    }
+  }
+  return ISVD_OK;
+}
+
+int64_t isvd_pool_slots(isvd_pool_t p) { return p ? (int64_t)p->streams.size() : 0; }
+
+isvd_status isvd_pool_gather_sigma(isvd_pool_t p, int32_t ld, double* out, int to_device) {
+  if (!p || !out || ld < 1) return ISVD_EINVAL;
+  const int64_t n = (int64_t)p->streams.size();
+  if (n == 0) return ISVD_OK;
+  double* dst = out;
+  if (!to_device) {
+    if (n * ld > p->gather_cap) {
+      cudaStreamSynchronize(p->stream);
+      if (p->gather_dev) cudaFree(p->gather_dev);
+      p->gather_dev = nullptr;
+      p->gather_cap = std::max<int64_t>(n * ld, 2 * p->gather_cap);
+      if (cudaMalloc((void**)&p->gather_dev, 8 * (size_t)p->gather_cap) != cudaSuccess) {
+        p->gather_cap = 0;
+        return pool_fail(p, ISVD_ENOMEM, "pool sigma gather buffer");
+      }
+    }
+    dst = p->gather_dev;
+  }
+  cudaError_t e = pool_gather_sigma_launch(n, p->stream, p->tab_sig, p->tab_st, ld, dst);
+  if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool sigma gather: ") + cudaGetErrorString(e));
+  p->launches++;
+  if (!to_device &&
+      cudaMemcpyAsync(out, p->gather_dev, 8 * (size_t)(n * ld), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool sigma gather copy");
   return ISVD_OK;
 }
 

@@ -35,7 +35,9 @@ cudaError_t pool_retry_set_attr();
 // Pool warp-per-update kernels k_pool_warp<kb> and row-parallel rotations k_pool_rotate<kb>
 // (kb = 8/16/32); scratch is the bucket run's first RotScratch<kb> record.
 cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
-                             void* scratch, const int* chunks, int* block_op);
+                             void* scratch, const int* chunks, int* block_op, int rot_rows);
+// Rows of one side per rotation block for rank bucket kb (the warp kernel's block tables).
+int pool_rot_rows(int kb, bool use_tc);
 // use_tc selects the tensor-core rotation (k_pool_rotate_tc, buckets 16 and 32).
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
                                const int* chunks, const int* block_op, bool use_tc);
@@ -45,5 +47,15 @@ cudaError_t pool_warp_set_attrs();
 // listed stream.
 struct PoolReorthOp;
 cudaError_t pool_reorth_launch(int count, cudaStream_t s, const PoolReorthOp* list, double tol);
+
+// Completion records of ops[0 .. count) (the state each op left behind, after its tick), and
+// the gather of many streams' singular values into one array (out[s * ld + c], zero-padded).
+struct PoolCompletion;
+struct PoolRankOp;
+// k <- min(k + 1, kcap) for every listed stream whose EVR = sum sigma^2 / N_t is below tau.
+cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau);
+cudaError_t pool_complete_launch(int count, cudaStream_t s, const PoolOp* ops, PoolCompletion* out);
+cudaError_t pool_gather_sigma_launch(int64_t n, cudaStream_t s, const double* const* sig, const DevState* const* st,
+                                     int ld, double* out);
 
 }  // namespace isvd

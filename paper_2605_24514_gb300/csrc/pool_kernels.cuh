@@ -24,7 +24,27 @@ struct PoolOp {
   double tol_rel;      // rank test threshold
   int32_t ld;          // row stride of U and V
   int32_t kind;        // kRow, kCol, kEntry
+  int32_t sid;         // pool stream id (completion records)
+  int32_t pad;
+  int64_t seq;         // pool-wide sequence number of the op (completion records)
 };
+
+// A stream whose adaptive-rank check is due (Eq. evr-rank-rule read as a growth rule).
+struct PoolRankOp {
+  DevState* st;
+  const double* sig;
+  int32_t kcap;  // the stream's rank capacity (its bucket, at most the pool's k_max)
+  int32_t pad;
+};
+
+// One completion record (layout of isvd_completion in include/isvd.h).
+struct PoolCompletion {
+  int64_t seq;
+  int32_t stream, kind, status, r;
+  double rho, sigma_max;
+  uint64_t done_ns;
+};
+
 
 constexpr int kPoolZMax = 4096;  // longest projection side handled by the fused kernel
 
@@ -32,7 +52,10 @@ __host__ __device__ constexpr int pool_threads(int kb) {
   return kb <= 8 ? 128 : kb <= 16 ? 256 : kb <= 32 ? 288 : 544;
 }
 // Rank bucket of the fused kernel for a stream of working-rank capacity k.
-__host__ __device__ constexpr int pool_bucket(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
+// Bucket 128 has no batched kernel: its updates run through the single-stream kernels, in order.
+__host__ __device__ constexpr int pool_bucket(int k) {
+  return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128;
+}
 
 template <int KB>
 __host__ __device__ inline size_t pool_smem_bytes() {

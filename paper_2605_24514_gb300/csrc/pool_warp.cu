@@ -10,10 +10,10 @@ namespace isvd {
 namespace {
 template <int KB>
 void warp_launch(int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n, void* scratch,
-                 const int* chunks, int* block_op) {
+                 const int* chunks, int* block_op, int rot_rows) {
   const int blocks = (count + kWarpsPerBlock - 1) / kWarpsPerBlock;
   k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), s>>>(
-      ops, count, base, retry, retry_n, reinterpret_cast<RotScratch<KB>*>(scratch), chunks, block_op);
+      ops, count, base, retry, retry_n, reinterpret_cast<RotScratch<KB>*>(scratch), chunks, block_op, rot_rows);
 }
 template <int KB>
 void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
@@ -30,14 +30,16 @@ void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void
 }  // namespace
 
 cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
-                             void* scratch, const int* chunks, int* block_op) {
+                             void* scratch, const int* chunks, int* block_op, int rot_rows) {
   switch (kb) {
-    case 8: warp_launch<8>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op); break;
-    case 16: warp_launch<16>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op); break;
-    default: warp_launch<32>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op); break;
+    case 8: warp_launch<8>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
+    case 16: warp_launch<16>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
+    default: warp_launch<32>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
   }
   return cudaGetLastError();
 }
+
+int pool_rot_rows(int kb, bool use_tc) { return use_tc && (kb == 16 || kb == 32) ? kTcRotRows : kPoolRotRows; }
 
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
                                const int* chunks, const int* block_op, bool use_tc) {
@@ -58,6 +60,67 @@ cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp
 cudaError_t pool_reorth_launch(int count, cudaStream_t s, const PoolReorthOp* list, double tol) {
   if (count <= 0) return cudaSuccess;
   k_pool_reorth<<<count, kReorthThreads, sizeof(ReorthSmem), s>>>(list, tol);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_pool_complete(const PoolOp* __restrict__ ops, int count, PoolCompletion* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const PoolOp& op = ops[q];
+  const DevState* st = op.st;
+  PoolCompletion c;
+  c.seq = op.seq;
+  c.stream = op.sid;
+  c.kind = op.kind;
+  const int status = st->status;
+  c.status = status & kStNonFinite ? 9 : status & kStNotConv ? 6 : status & kStTimeout ? 7 : 0;  // isvd_status
+  c.r = st->r;
+  c.rho = op.kind == kEntry ? 0.0 : st->rho;
+  c.sigma_max = st->r > 0 ? op.sig[0] : 0.0;
+  c.done_ns = tc::globaltimer_ns();
+  out[q] = c;
+}
+
+__global__ void k_pool_gather_sigma(const double* const* __restrict__ sig, const DevState* const* __restrict__ st,
+                                    int64_t n, int ld, double* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * ld) return;
+  const int64_t s = idx / ld;
+  const int c = (int)(idx - s * ld);
+  out[idx] = c < st[s]->r ? sig[s][c] : 0.0;
+}
+// Adaptive rank (Eq. evr-rank-rule as a growth rule), one thread per listed stream.
+__global__ void k_pool_rank(const PoolRankOp* __restrict__ list, int count, double tau) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const PoolRankOp op = list[q];
+  DevState* st = op.st;
+  const int r = st->r;
+  double ss = 0.0;
+  for (int c = 0; c < r; ++c) ss += op.sig[c] * op.sig[c];
+  const double N = st->N;
+  if (N > 0.0 && ss / N < tau && st->k < op.kcap) st->k += 1;
+}
+}  // namespace
+
+cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau) {
+  if (count <= 0) return cudaSuccess;
+  k_pool_rank<<<(count + 127) / 128, 128, 0, s>>>(list, count, tau);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_complete_launch(int count, cudaStream_t s, const PoolOp* ops, PoolCompletion* out) {
+  if (count <= 0) return cudaSuccess;
+  k_pool_complete<<<(count + 127) / 128, 128, 0, s>>>(ops, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_gather_sigma_launch(int64_t n, cudaStream_t s, const double* const* sig, const DevState* const* st,
+                                     int ld, double* out) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t tot = n * ld;
+  k_pool_gather_sigma<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(sig, st, n, ld, out);
   return cudaGetLastError();
 }
 

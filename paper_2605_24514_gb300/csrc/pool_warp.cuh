@@ -602,14 +602,15 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
 
 // ops[0 .. count): row/column appends of streams in rank bucket KB, one warp each. Updates that
 // need the CTA kernel are listed in retry[] as base + index (count in *retry_n), untouched.
-// Also fills block_op[chunk_start[e] + i] = e for the update's rotation blocks.
+// Also fills block_op[chunk_start[e] + i] = e for the update's rotation blocks (rot_rows rows of
+// one side per block: 256 for the FP32-pipe rotation, 128 for the tensor-core one).
 constexpr int kPoolRotThreads = 128;
 constexpr int kPoolRotRows = 2 * kPoolRotThreads;  // rows per rotation block (two per thread)
 template <int KB>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
     k_pool_warp(const PoolOp* __restrict__ ops, int count, int base, int* __restrict__ retry,
                 int* __restrict__ retry_n, RotScratch<KB>* __restrict__ scratch, const int* __restrict__ chunk_start,
-                int* __restrict__ block_op) {
+                int* __restrict__ block_op, int rot_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wid = threadIdx.x >> 5;
   const int e = blockIdx.x * kWarpsPerBlock + wid;
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
   const PoolOp op = ops[e];
   {
     const int64_t nP = op.kind == kRow ? op.n : op.m, nQ = op.kind == kRow ? op.m : op.n;
-    const int nb = (int)((nP + kPoolRotRows - 1) / kPoolRotRows + (nQ + kPoolRotRows - 1) / kPoolRotRows);
+    const int nb = (int)((nP + rot_rows - 1) / rot_rows + (nQ + rot_rows - 1) / rot_rows);
     const int c0 = chunk_start[e];
     for (int i = threadIdx.x & 31; i < nb; i += 32) block_op[c0 + i] = e;
   }

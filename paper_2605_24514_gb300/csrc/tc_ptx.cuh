@@ -146,6 +146,32 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       : "memory");
 }
 
+// Instruction descriptor of a dense kind::f16 MMA with BF16 A and B (both K-major) and FP32
+// accumulation: D format F32 (bits 4-5 = 1), A and B format BF16 (bits 7-9 and 10-12 = 1).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem], BF16 operands, FP32 accumulator (single thread issues).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Byte offset of element (row, kk) in a K-major no-swizzle operand tile of 16-bit elements with
+// K columns: 8-row x 16-byte core matrices (8 elements per core-matrix row), 128 bytes apart
+// along K, 8-row groups K * 16 bytes apart.
+__host__ __device__ constexpr uint32_t kmajor_offset16(int row, int kk, int K) {
+  return (uint32_t)((row >> 3) * (K * 16) + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+}
+
 // Arrives on bar once every MMA this thread issued before has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

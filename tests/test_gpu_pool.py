@@ -305,3 +305,62 @@ def test_pool_tensor_core_rotation_matches_fp32_pipes(isvd, k):
         assert np.abs(V.T.astype(np.float64) @ V - np.eye(V.shape[1])).max() < 1e-5
     for p in pools:
         p.close()
+
+
+def test_pool_completion_records_and_sigma_gather(isvd):
+    """isvd_pool_poll returns one record per op, each op exactly once and a stream's ops in its
+    order; the records carry the rank, residual norm (Eq. row-residual) and sigma_1 each op left
+    behind, checked against the oracle op by op. isvd_pool_gather_sigma returns every slot's
+    singular values in one array."""
+    data = make_streams(7, seed=21, n_events=9, ks=(4, 8, 16, 32), nrange=(30, 120))
+    pool = isvd.Pool(k_max=32, flags=isvd.POOL_COMPLETIONS)
+    factors = [oracle.truncated_svd(A0.astype(np.float64), k) for A0, _, k in data]
+    ids = [pool.admit(A0, k, factors=f) for (A0, _, k), f in zip(data, factors)]
+    ops, payload = interleave(ids, data)
+    half = len(ops) // 2
+    # two submits (seq continues across them); the second payload slice is rebased to 0
+    base = min((o[5] for o in ops[half:] if o[1] != streams.ENTRY), default=0)
+    ops2 = [(o[0], o[1], o[2], o[3], o[4], o[5] - base if o[1] != streams.ENTRY else 0, o[6]) for o in ops[half:]]
+    pool.submit(ops[:half], payload)
+    pool.submit(ops2, payload[base:])
+    pool.sync()
+    rec = pool.poll()
+    assert rec.size == len(ops)
+    assert sorted(rec["seq"].tolist()) == list(range(len(ops)))
+    assert pool.poll().size == 0                      # every record is handed out once
+    by_seq = {int(r["seq"]): r for r in rec}
+    for sidx, ((A0, ev, k), f) in enumerate(zip(data, factors)):
+        o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
+        seqs = [q for q, op in enumerate(ops) if op[0] == ids[sidx]]
+        assert len(seqs) == len(ev)
+        for e, q in enumerate(seqs):
+            kd = int(ev.kind[e])
+            if kd == streams.ENTRY:
+                o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+            else:
+                o.apply(kd, ev.vector(e).astype(np.float32).astype(np.float64))
+            r = by_seq[q]
+            assert r["stream"] == ids[sidx] and r["kind"] == kd and r["status"] == 0
+            assert r["r"] == o.r
+            assert abs(r["sigma_max"] - o.s[0]) <= 1e-5 * o.s[0]
+            if kd == streams.ENTRY:
+                assert r["rho"] == 0.0
+            else:
+                assert abs(r["rho"] - o.rho_last) <= 1e-4 * max(o.rho_last, 1e-3 * o.s[0])
+        done = [int(by_seq[q]["done_ns"]) for q in seqs]
+        assert done == sorted(done)                   # a stream's ops complete in its order
+    G = pool.gather_sigma(32)
+    assert G.shape == (pool.slots, 32)
+    for sidx, sid in enumerate(ids):
+        s = pool.stream(sid).sigma()
+        np.testing.assert_array_equal(G[sid, :s.size], s)
+        assert np.all(G[sid, s.size:] == 0.0)
+    pool.release(ids[0])
+    G2 = pool.gather_sigma(8)
+    assert np.all(G2[ids[0]] == 0.0)
+    plain = isvd.Pool(k_max=8)
+    with pytest.raises(isvd.IsvdError) as e:
+        plain.poll()
+    assert e.value.name == "EINVAL"
+    plain.close()
+    pool.close()
