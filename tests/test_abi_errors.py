@@ -69,7 +69,7 @@ def test_noalloc_rejects_arguments_before_device_work(pkg):
 def test_pool_rejects_arguments_before_device_work(pkg):
     L = pkg.lib()
     h = C.c_void_p()
-    for k_max in (0, 65):
+    for k_max in (0, 129):
         cfg = pkg.PoolConfig(k_max=k_max)
         assert L.isvd_pool_create(C.byref(cfg), C.byref(h)) == EINVAL
         assert not h.value
