@@ -43,6 +43,12 @@ WORKLOADS = {
                          desc="4096 independent factor-model streams, n ~ U[50,500], m0 = 2n, k ~ {8,16,32}, "
                               "one row append per stream per tick, FP32 bulk + FP64-class core; batched pool path "
                               "vs per-stream single-stream kernels (plain GPU form)"),
+    "serving": dict(prec="fp32", streams=2000, n_lo=100, n_hi=2000, k_lo=8, k_hi=64, mix=(0.6, 0.1, 0.3),
+                    rate=1e6, requests=200_000, budget_gb_per_20000=120.0, rank_every=100, tau_evr=0.9, f=10,
+                    desc="serving loop: streams with n log-uniform in [100, 2000], m0 = 2n, k uniform in [8, 64], "
+                         "Poisson arrivals, row/col/entry 60/10/30, admission under an HBM budget (120 GB per "
+                         "20,000 streams), adaptive rank (EVR < 0.9, capped at each stream's rank bucket), "
+                         "continuous batching: each submit takes the requests that have arrived"),
     "panel-200x50-k10": dict(prec="fp64", check_every=50, T_refresh=250, batch=200,
                              desc="200x50 factor panel (5 factors), k=10, 1000 row appends then 200 entry "
                                   "updates, FP64, periodic refresh 250, metrics every 50"),
@@ -504,9 +510,10 @@ def run_batched(args):
                    "plain_form_ticks": plain_ticks, "plain_form_tick_ms_min_max": plain_spread,
                    "speedup_vs_plain": round(value / plain_value, 2) if plain_value else None,
                    "l2": "working set per tick larger than L2 (no flush needed)",
-                   "latency_us": {"p50": round(float(np.percentile(lat_ms, 50)) * 1e3, 1),
-                                  "p99": round(float(np.percentile(lat_ms, 99)) * 1e3, 1),
-                                  "max": round(float(lat_ms.max()) * 1e3, 1), "ticks": int(lat_ms.size),
+                   "latency_us": {"p50": round(float(np.percentile(lat_ms, 50)) * 1e3, 1) if lat_ms.size else None,
+                                  "p99": round(float(np.percentile(lat_ms, 99)) * 1e3, 1) if lat_ms.size else None,
+                                  "max": round(float(lat_ms.max()) * 1e3, 1) if lat_ms.size else None,
+                                  "ticks": int(lat_ms.size),
                                   "note": "device time of a tick, measured alone; every update of a tick "
                                           "completes with it"},
                    "err_ratio_gpu_sample": [round(float(r), 6) for r in gpu_ratios],
@@ -537,6 +544,177 @@ def run_batched(args):
             "ok": bool(all(np.isfinite(gpu_ratios)) and max(gpu_ratios) <= 1.05 and max(rel) <= 0.01),
             "rule": "every sampled ratio finite and <= 1.05, and within 1% of the oracle's on the same stream"}
     return out
+
+
+def _serving_inputs(W, S, N, seed, torch):
+    """Synthetic serving workload, drawn on the device with torch (input generation only): per stream
+    a factor-model panel A0 (2n x n), and the scripted requests that the Poisson arrivals draw from:
+    rows x = B f + eps, new assets y = F b + eps over the stream's factor history, entry increments
+    delta ~ N(0, 0.005) at uniform positions. Returns panels, stream parameters, the arrival-ordered
+    request table and one device payload buffer."""
+    dev = "cuda"
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = W["f"]
+    ns = np.exp(rng.uniform(np.log(W["n_lo"]), np.log(W["n_hi"]), size=S)).astype(np.int64)
+    ks = rng.integers(W["k_lo"], W["k_hi"] + 1, size=S)
+    arr = np.cumsum(rng.exponential(1.0 / W["rate"], size=N))        # arrival times (s)
+    who = rng.integers(0, S, size=N)                                  # stream of each arrival
+    kinds = rng.choice(3, size=N, p=np.asarray(W["mix"]))
+    vol = torch.tensor(0.02 * 0.7 ** np.arange(f), device=dev, dtype=torch.float32)
+
+    def noise(shape):
+        z = torch.randn(shape, generator=g, device=dev)
+        c = torch.distributions.Chi2(torch.tensor(4.0, device=dev)).sample(shape)
+        return 0.01 * z / torch.sqrt(c / 4.0)
+
+    panels, pay, offs, lens = [], [], np.zeros(N, np.int64), np.zeros(N, np.int64)
+    ii, jj, dd = np.zeros(N, np.int64), np.zeros(N, np.int64), np.zeros(N)
+    pos = 0
+    order = np.argsort(who, kind="stable")
+    bounds = np.searchsorted(who[order], np.arange(S + 1))
+    for sidx in range(S):
+        n = int(ns[sidx])
+        mine = order[bounds[sidx]:bounds[sidx + 1]]                   # this stream's arrivals, in order
+        n_rows = int(np.sum(kinds[mine] == 0))
+        B = torch.randn((n, f), generator=g, device=dev) / np.sqrt(f)
+        Fh = torch.randn((2 * n + n_rows, f), generator=g, device=dev) * vol
+        panels.append((Fh[:2 * n] @ B.T + noise((2 * n, n))).contiguous())
+        rows = Fh[2 * n:] @ B.T + noise((n_rows, n))
+        m, ncol, ri = 2 * n, n, 0
+        for q in mine:
+            kd = int(kinds[q])
+            if kd == 0:
+                v = rows[ri, :ncol] if ncol == n else torch.cat(
+                    [rows[ri], torch.randn(ncol - n, generator=g, device=dev) * 0.01])
+                ri += 1
+                m += 1
+            elif kd == 1:
+                b = torch.randn((f,), generator=g, device=dev) / np.sqrt(f)
+                v = Fh[:m] @ b + noise((m,)) if m <= Fh.shape[0] else None
+                if v is None:
+                    kinds[q] = 2
+                    kd = 2
+                else:
+                    ncol += 1
+            if kd == 2:
+                ii[q], jj[q], dd[q] = rng.integers(0, m), rng.integers(0, ncol), 0.005 * rng.standard_normal()
+                continue
+            pay.append(v.reshape(-1))
+            offs[q], lens[q] = pos, v.numel()
+            pos += v.numel()
+    payload = torch.cat(pay) if pay else torch.zeros(1, device=dev)
+    return panels, ns, ks, arr, who, kinds, offs, lens, ii, jj, dd, payload
+
+
+def run_serving(args):
+    """Serving loop with continuous batching: Poisson arrivals over many streams; every pass of the
+    host loop submits the requests that have arrived since the previous pass (one submit, which the
+    pool splits into ticks so that a stream's requests keep their order) and polls completion
+    records. Latency of a request = its completion (device clock mapped to the host clock) minus its
+    arrival time. The timed quantity is the whole run: requests / (last completion - first arrival)."""
+    import torch
+
+    import paper_2605_24514_gb300 as pkg
+    from paper_2605_24514_gb300 import build as b
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    W = WORKLOADS["serving"]
+    S = args.streams or W["streams"]
+    N = args.requests or W["requests"]
+    rate = args.rate or W["rate"]
+    W = dict(W, rate=rate)
+    t_setup = time.perf_counter()
+    panels, ns, ks, arr, who, kinds, offs, lens, ii, jj, dd, payload = _serving_inputs(W, S, N, rank_seed(rank), torch)
+    budget = int(W["budget_gb_per_20000"] * 2**30 * S / 20000)
+    st = torch.cuda.Stream()
+    pool = pkg.Pool(k_max=int(W["k_hi"]), hbm_budget_bytes=budget, stream=st.cuda_stream,
+                    flags=pkg.POOL_COMPLETIONS, rank_every=W["rank_every"], tau_evr=W["tau_evr"])
+    ids = np.full(S, -1, np.int64)
+    cap_extra = np.bincount(who, minlength=S)
+    for sidx in range(S):
+        A0 = panels[sidx]
+        m0, n0 = A0.shape
+        try:
+            ids[sidx] = pool.admit_device(A0, int(ks[sidx]), row_cap=m0 + int(cap_extra[sidx]) + 2,
+                                          col_cap=n0 + int(cap_extra[sidx]) + 2)
+        except pkg.IsvdError as e:
+            if e.name != "EBUDGET":
+                raise
+    del panels
+    admitted = ids >= 0
+    keep = admitted[who]                       # requests of refused streams are dropped
+    arr, who, kinds, offs, lens = arr[keep], who[keep], kinds[keep], offs[keep], lens[keep]
+    ii, jj, dd = ii[keep], jj[keep], dd[keep]
+    N = int(arr.size)
+    op_t = np.dtype([("stream", np.int32), ("kind", np.int32), ("i", np.int64), ("j", np.int64),
+                     ("delta", np.float64), ("off", np.int64), ("len", np.int64)])
+    ops = np.zeros(N, op_t)
+    ops["stream"], ops["kind"], ops["i"], ops["j"] = ids[who], kinds, ii, jj
+    ops["delta"], ops["off"], ops["len"] = dd, offs, lens
+    pool.sync()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    # Clock mapping: host monotonic ns = device globaltimer ns + offset, offset taken as the smallest
+    # (host time a record was seen - its device stamp) over the run (records seen right away).
+    done_dev = np.zeros(N, np.uint64)
+    seen_host = np.zeros(N, np.int64)
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter_ns()
+    i = n_done = 0
+    submits = 0
+    while n_done < N:
+        now = (time.perf_counter_ns() - t0) * 1e-9
+        j = int(np.searchsorted(arr, now, side="right"))
+        if j > i:
+            seg = ops[i:j]
+            pool.submit_raw(seg.ctypes.data, j - i, payload.data_ptr(), int(payload.numel()), 1)
+            submits += 1
+            i = j
+        rec = pool.poll()
+        if rec.size:
+            h = time.perf_counter_ns()
+            q = rec["seq"]
+            done_dev[q] = rec["done_ns"]
+            seen_host[q] = h
+            n_done += rec.size
+            assert np.all(rec["status"] == 0), "device error in a served request"
+    clk = clocks.stop()
+    pool.sync()
+    offset = int(np.min(seen_host - done_dev.astype(np.int64)))
+    done_host = done_dev.astype(np.int64) + offset
+    lat_us = (done_host - t0 - (arr * 1e9).astype(np.int64)) / 1e3
+    span_s = (done_host.max() - t0) * 1e-9 - float(arr[0])
+    value = N / span_s
+    kk = np.array([pool.stream(int(x)).shape()[3] for x in ids[admitted]])
+    out = {
+        "metric": "iSVD updates/s and p50/p99 update latency at err ratio<=1.05 vs plain GPU form",
+        "value": round(value, 1), "unit": "updates/s", "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": round(span_s * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (factor-model panels and requests drawn on the device)",
+        "config": {"workload": "serving", "desc": W["desc"], "streams": S, "streams_admitted": int(admitted.sum()),
+                   "hbm_budget_bytes": budget, "pool_bytes_used": pool.bytes_used, "requests": N,
+                   "offered_rate_per_s": rate, "submits": submits,
+                   "kind_mix": {k: int(np.sum(kinds == c)) for c, k in enumerate(("row", "col", "entry"))},
+                   "latency_us": {"p50": round(float(np.percentile(lat_us, 50)), 1),
+                                  "p99": round(float(np.percentile(lat_us, 99)), 1),
+                                  "max": round(float(lat_us.max()), 1),
+                                  "note": "arrival (Poisson schedule, host clock) to the op's completion record "
+                                          "(device clock mapped to the host clock)"},
+                   "k_final_mean": round(float(kk.mean()), 2) if kk.size else None,
+                   "setup_s": round(setup_s, 1)},
+        "gpu_launches": int(pool.launches),
+        "clocks": clk,
+    }
+    pool.close()
+    return out if rank == 0 else None
 
 
 def _batched_sample(args, n_streams, ticks):
@@ -696,6 +874,8 @@ def main():
     ap.add_argument("--plain-ticks", type=int, default=3)
     ap.add_argument("--lat-ticks", type=int, default=100)
     ap.add_argument("--acc-streams", type=int, default=8)
+    ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests per second")
     ap.add_argument("--simt-rotations", action="store_true",
                     help="batched workload: rotate on the FP32 pipes in every rank bucket")
     args = ap.parse_args()
@@ -703,6 +883,8 @@ def main():
         out = run_reference(args)
     elif args.workload.startswith("batched"):
         out = run_batched(args)
+    elif args.workload == "serving":
+        out = run_serving(args)
     else:
         out = run_gb300(args)
     if out is not None:

@@ -370,6 +370,59 @@ isvd_status isvd_pool_profile_read(isvd_pool_t p, double* ms_out, int64_t* launc
  * n <= 4 entries. *submits (may be NULL) receives the number of submits counted. */
 isvd_status isvd_pool_host_profile(isvd_pool_t p, double* us_out, int n, int64_t* submits);
 
+/* --- finance layer (Section 5) --------------------------------------------------------------
+ * Causal centering of return rows before they are appended (Section 5.1), and the low-rank
+ * covariance and portfolio risk implied by a handle's factors (Section 5.3). */
+
+#define ISVD_CENTER_CAUSAL 1  /* expanding mean, Option A: mu_t = mu_{t-1} + (r_t - mu_{t-1}) / t */
+#define ISVD_CENTER_EW 2      /* exponentially weighted mean, Option B: mu_t = (1 - a) mu_{t-1} + a r_t */
+
+typedef struct isvd_center_ctx* isvd_center_t;
+
+/* Centering state for n assets (mu = 0, no rows yet), arithmetic in FP64, rows of the storage type of
+ * prec (double for ISVD_FP64, float for ISVD_FP32), work queued on cuda_stream. alpha is Option B's
+ * forgetting factor in (0, 1) (ignored for ISVD_CENTER_CAUSAL). ISVD_EINVAL for a bad mode, alpha, n or
+ * prec; ISVD_ENOMEM if the state cannot be allocated. */
+isvd_status isvd_center_create(int32_t mode, double alpha, int64_t n, int32_t prec, void* cuda_stream,
+                               isvd_center_t* out);
+void isvd_center_destroy(isvd_center_t c);
+
+/* Centers `rows` raw return rows in time order (row stride ld_raw >= n) into out (row stride
+ * ld_out >= n): out_t = r_t - mu_t with mu_t updated by row t first, so each row is centered with
+ * the returns up to and including its own. Both buffers are device memory (on_device = 1) or host
+ * memory (copied through the state's staging buffer; the call returns when out is written). The
+ * state advances by `rows`. */
+isvd_status isvd_center_rows(isvd_center_t c, const void* raw, int64_t rows, int64_t ld_raw, void* out,
+                             int64_t ld_out, int on_device);
+
+/* New assets (columns appended to the returns matrix): their current means (count host doubles). */
+isvd_status isvd_center_add_assets(isvd_center_t c, const double* mu_new, int64_t count);
+
+/* Copies the n current means into host memory (mu may be NULL) and the number of rows centered. */
+isvd_status isvd_center_state(isvd_center_t c, double* mu, int64_t* count);
+
+/* Low-rank covariance and portfolio risk of a handle, Section 5.3: with t = m rows of the centered
+ * returns matrix, S_inc = V diag(sigma^2) V^T / (t - 1) (Eq. low-rank-covariances) and the portfolio
+ * volatility vol = sqrt(w^T S_inc w) (Eq. portfolio-vol) for weights w (n values of the storage type,
+ * host or device memory; NULL selects the equal-weight portfolio 1/n). With ISVD_RISK_FULL also the
+ * same quantities for the optimal rank-r factorisation of A_t (the truncated SVD of the metrics),
+ * the risk error |vol - vol_opt| / vol_opt (Eq. risk-error) and the covariance error
+ * ||S_inc - S_opt||_F / ||S_opt||_F (Eq. cov-error), computed from r x r Gram matrices of the factors
+ * without forming an n x n matrix. Synchronises. */
+#define ISVD_RISK_CHEAP 0
+#define ISVD_RISK_FULL 1
+typedef struct {
+  int64_t t;          /* rows of the centered returns matrix */
+  int32_t r;          /* rank of the factors */
+  int32_t reserved;
+  double vol;         /* sqrt(w^T S_inc w) */
+  double vol_opt;     /* sqrt(w^T S_opt w) (ISVD_RISK_FULL), NaN otherwise */
+  double risk_error;  /* |vol - vol_opt| / vol_opt (ISVD_RISK_FULL), NaN otherwise */
+  double cov_error;   /* ||S_inc - S_opt||_F / ||S_opt||_F (ISVD_RISK_FULL), NaN otherwise */
+  double cov_norm;    /* ||S_inc||_F */
+} isvd_risk_t;
+isvd_status isvd_risk(isvd_t h, const void* w, int w_on_device, int flags, isvd_risk_t* out);
+
 /* --- allocation-free orthogonality measurement ----------------------------------------------
  * The paper has no counterpart: this is a library service for callers that cannot allocate
  * device memory, e.g. code running under a memory pool that forbids new allocations, code that

@@ -69,6 +69,8 @@ class PoolConfig(C.Structure):
 
 POOL_SIMT_ROTATIONS = 1
 POOL_COMPLETIONS = 2
+COMPLETION_DTYPE = np.dtype([("seq", np.int64), ("stream", np.int32), ("kind", np.int32), ("status", np.int32),
+                             ("r", np.int32), ("rho", np.float64), ("sigma_max", np.float64), ("done_ns", np.uint64)])
 
 
 class Completion(C.Structure):
@@ -79,6 +81,18 @@ class Completion(C.Structure):
 class PoolOp(C.Structure):
     _fields_ = [("stream", C.c_int32), ("kind", C.c_int32), ("i", C.c_int64), ("j", C.c_int64),
                 ("delta", C.c_double), ("off", C.c_int64), ("len", C.c_int64)]
+
+
+class Risk(C.Structure):
+    _fields_ = [("t", C.c_int64), ("r", C.c_int32), ("reserved", C.c_int32), ("vol", C.c_double),
+                ("vol_opt", C.c_double), ("risk_error", C.c_double), ("cov_error", C.c_double),
+                ("cov_norm", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+CENTER_CAUSAL, CENTER_EW = 1, 2
 
 
 class Event(C.Structure):
@@ -131,6 +145,13 @@ _SIGS = {
     "isvd_pool_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
     "isvd_pool_host_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int64)]),
     "isvd_pool_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "isvd_risk": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(Risk)]),
+    "isvd_center_create": (C.c_int, [C.c_int32, C.c_double, C.c_int64, C.c_int32, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "isvd_center_destroy": (None, [C.c_void_p]),
+    "isvd_center_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int]),
+    "isvd_center_add_assets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "isvd_center_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "isvd_pool_slots": (C.c_int64, [C.c_void_p]),
     "isvd_pool_gather_sigma": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int]),
 }
@@ -279,6 +300,17 @@ class ISVD:
         self._check(lib().isvd_get_matrix(self._h, A.ctypes.data, 0), "get_matrix")
         return A
 
+    def risk(self, w=None, full=True):
+        """Low-rank covariance and portfolio risk of Section 5.3 (isvd_risk); ``w`` None = 1/n."""
+        out = Risk()
+        if w is None:
+            p, d = None, 0
+        else:
+            w = self._vec(w)
+            p, d = _ptr(w)
+        self._check(lib().isvd_risk(self._h, p, d, 1 if full else 0, C.byref(out)), "risk")
+        return out.as_dict()
+
     def reorthogonalize(self, force=False):
         eu, ev = C.c_double(), C.c_double()
         self._check(lib().isvd_reorthogonalize(self._h, int(force), C.byref(eu), C.byref(ev)), "reorthogonalize")
@@ -327,6 +359,63 @@ class ISVD:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Centering:
+    """Causal centering of return rows (Section 5.1, isvd_center_*): CENTER_CAUSAL (expanding mean)
+    or CENTER_EW (exponentially weighted mean with forgetting factor ``alpha``)."""
+
+    def __init__(self, n, mode=CENTER_CAUSAL, alpha=0.0, prec=FP64, stream=None):
+        self.prec = prec
+        self.dtype = np.float64 if prec == FP64 else np.float32
+        h = C.c_void_p()
+        self._c = None
+        st = lib().isvd_center_create(int(mode), float(alpha), int(n), int(prec), stream or 0, C.byref(h))
+        if st:
+            raise IsvdError(st, "isvd_center_create")
+        self._c = h
+        self.n = int(n)
+
+    def rows(self, raw):
+        """Centers the rows of ``raw`` (rows x n, host array or CUDA tensor) in time order."""
+        if isinstance(raw, np.ndarray):
+            raw = np.ascontiguousarray(raw, dtype=self.dtype)
+            out = np.empty_like(raw)
+        else:
+            out = raw.new_empty(raw.shape)
+        rows, n = raw.shape
+        p, d = _ptr(raw)
+        q, _ = _ptr(out)
+        st = lib().isvd_center_rows(self._c, p, rows, n, q, n, d)
+        if st:
+            raise IsvdError(st, "isvd_center_rows")
+        return out
+
+    def add_assets(self, mu_new):
+        mu_new = np.ascontiguousarray(mu_new, dtype=np.float64)
+        st = lib().isvd_center_add_assets(self._c, mu_new.ctypes.data, mu_new.size)
+        if st:
+            raise IsvdError(st, "isvd_center_add_assets")
+        self.n += mu_new.size
+
+    def state(self):
+        mu = np.empty(self.n, np.float64)
+        cnt = C.c_int64()
+        st = lib().isvd_center_state(self._c, mu.ctypes.data, C.byref(cnt))
+        if st:
+            raise IsvdError(st, "isvd_center_state")
+        return mu, cnt.value
+
+    def close(self):
+        if self._c:
+            lib().isvd_center_destroy(self._c)
+            self._c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _Borrowed(ISVD):
@@ -378,6 +467,15 @@ class Pool:
         self._check(st, "isvd_pool_admit")
         return sid.value
 
+    def admit_device(self, A0, k, row_cap=0, col_cap=0):
+        """Admits a stream from a contiguous FP32 CUDA tensor A0 (m0 x n0), computing its truncated SVD."""
+        m0, n0 = A0.shape
+        sid = C.c_int32()
+        st = lib().isvd_pool_admit(self._p, A0.data_ptr(), m0, n0, n0, int(k), row_cap, col_cap, None, None,
+                                   None, 1, C.byref(sid))
+        self._check(st, "isvd_pool_admit")
+        return sid.value
+
     def release(self, sid):
         self._check(lib().isvd_pool_release(self._p, int(sid)), "isvd_pool_release")
 
@@ -416,12 +514,10 @@ class Pool:
     def poll(self, cap=1 << 16):
         """Completion records of finished ops not returned before (pool made with POOL_COMPLETIONS),
         as a NumPy structured array (fields of isvd_completion)."""
-        buf = (Completion * max(cap, 1))()
+        out = np.empty(max(cap, 1), dtype=COMPLETION_DTYPE)
         n = C.c_int64()
-        self._check(lib().isvd_pool_poll(self._p, buf, cap, C.byref(n)), "isvd_pool_poll")
-        dt = np.dtype([("seq", np.int64), ("stream", np.int32), ("kind", np.int32), ("status", np.int32),
-                       ("r", np.int32), ("rho", np.float64), ("sigma_max", np.float64), ("done_ns", np.uint64)])
-        return np.frombuffer(bytes(buf)[:n.value * C.sizeof(Completion)], dtype=dt).copy()
+        self._check(lib().isvd_pool_poll(self._p, out.ctypes.data, cap, C.byref(n)), "isvd_pool_poll")
+        return out[:n.value]
 
     @property
     def slots(self):

@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libisvd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # One translation unit per heavy kernel family, compiled concurrently, then linked.
 SOURCES = ["pool_tick64.cu", "pool_tick32.cu", "pool_retry.cu", "pool_tick16.cu", "pool_tick8.cu", "core_f32.cu",
-           "isvd.cu", "pool_warp.cu", "core_f64.cu", "noalloc.cu"]
+           "isvd.cu", "pool_warp.cu", "core_f64.cu", "noalloc.cu", "finance.cu"]
 OBJDIR = os.path.join(HERE, "_build")
 
 

@@ -45,6 +45,11 @@ struct isvd_ctx {
   int64_t orth_every = 0, since_orth = 0;
   int orth_on_device = 0;  // the batched path's monitor (DevState orth_u/v, reorths) runs this stream
   int64_t since_rank = 0;  // the batched path's adaptive-rank cadence
+  // finance layer scratch: weights (n, storage type) and the r x r Grams / vectors (FP64)
+  void* wbuf = nullptr;
+  int64_t wbuf_cap = 0;
+  double* riskbuf = nullptr;
+  int64_t risk_cap = 0;
   void* Uref = nullptr;
   int64_t m_ref = 0, uref_cap = 0;
   int r_ref = 0;
@@ -886,6 +891,69 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   return ISVD_OK;
 }
 
+// ---- finance layer: low-rank covariance and portfolio risk (Section 5.3) --------------------
+
+template <typename T>
+isvd_status do_risk(isvd_ctx* h, const void* w, int w_dev, int flags, isvd_risk_t* out) {
+  isvd_status s;
+  DevState ds;
+  if ((s = read_state(h, &ds))) return s;
+  const int r = ds.r;
+  const int64_t n = h->n;
+  memset(out, 0, sizeof(*out));
+  out->t = h->m;
+  out->r = r;
+  if (r < 1 || h->m < 2) return fail(h, ISVD_ESHAPE, "risk needs at least two rows and one component");
+  const T* wd = (const T*)w;
+  if (!w || !w_dev) {
+    if ((s = ensure_buf(h, &h->wbuf, &h->wbuf_cap, n * (int64_t)h->es))) return s;
+    if (!w) {
+      k_fill<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>((T*)h->wbuf, n, (T)(1.0 / (double)n));
+      CKL(h);
+    } else {
+      CK(h, cudaMemcpyAsync(h->wbuf, w, (size_t)n * h->es, cudaMemcpyHostToDevice, h->stream));
+    }
+    wd = (const T*)h->wbuf;
+  }
+  const int full = (flags & ISVD_RISK_FULL) != 0;
+  if (full && !(h->opt_t == h->t && h->opt_rank == r && h->Uopt && h->Vopt)) {
+    if ((s = ensure_buf(h, &h->Uopt, &h->uopt_cap, h->m * h->ld * (int64_t)h->es))) return s;
+    if ((s = ensure_buf(h, &h->Vopt, &h->vopt_cap, h->n * h->ld * (int64_t)h->es))) return s;
+    if ((s = tsvd<T>(h, r, (T*)h->Uopt, h->sig_opt, (T*)h->Vopt))) return s;
+    h->opt_t = h->t;
+    h->opt_rank = r;
+  }
+  const int64_t need = (int64_t)(3 * r * r + 2 * r + 8) * 8;
+  if ((s = ensure_buf(h, (void**)&h->riskbuf, &h->risk_cap, need))) return s;
+  double* G1 = h->riskbuf;
+  double* G2 = G1 + r * r;
+  double* Cx = G2 + r * r;
+  double* g = Cx + r * r;
+  double* gopt = g + r;
+  double* res = gopt + r;
+  const T* V = (const T*)h->V;
+  if ((s = gemm_tn<T>(h, V, h->ld, r, wd, 1, 1, n, g, true))) return s;
+  if ((s = gemm_tn<T>(h, V, h->ld, r, V, h->ld, r, n, G1, true))) return s;
+  if (full) {
+    const T* Vo = (const T*)h->Vopt;
+    if ((s = gemm_tn<T>(h, Vo, h->ld, r, wd, 1, 1, n, gopt, true))) return s;
+    if ((s = gemm_tn<T>(h, Vo, h->ld, r, Vo, h->ld, r, n, G2, true))) return s;
+    if ((s = gemm_tn<T>(h, V, h->ld, r, Vo, h->ld, r, n, Cx, true))) return s;
+  }
+  k_risk_finish<<<1, 256, 0, h->stream>>>(h->sig, h->sig_opt, g, gopt, G1, G2, Cx, r, 1.0 / (double)(h->m - 1), full,
+                                          res);
+  CKL(h);
+  double v[5];
+  CK(h, cudaMemcpyAsync(v, res, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  out->vol = v[0];
+  out->vol_opt = v[1];
+  out->risk_error = v[2];
+  out->cov_error = v[3];
+  out->cov_norm = v[4];
+  return ISVD_OK;
+}
+
 // ---- re-orthogonalisation -----------------------------------------------------------------
 
 template <typename T>
@@ -1153,7 +1221,7 @@ void isvd_destroy(isvd_t h) {
   cudaStreamSynchronize(h->stream);
   void* bufs[] = {h->U, h->V, h->A, h->Uref, h->st, h->sig, h->p, h->part, h->UK, h->VK, h->xbuf, h->G,
                   h->small, h->evals, h->inv, h->scal, h->info, h->Rtmp, h->Uopt, h->Vopt, h->sig_opt, h->Cbuf,
-                  h->Yb, h->Om, h->Zd, h->Rl};
+                  h->Yb, h->Om, h->Zd, h->Rl, h->wbuf, h->riskbuf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1298,6 +1366,17 @@ isvd_status isvd_reorthogonalize(isvd_t h, int force, double* err_u, double* err
   if (!h) return ISVD_EINVAL;
   if (h->sticky) return (isvd_status)h->sticky;
   return h->prec == ISVD_FP64 ? do_reorth<double>(h, force, err_u, err_v) : do_reorth<float>(h, force, err_u, err_v);
+}
+
+isvd_status isvd_risk(isvd_t h, const void* w, int w_on_device, int flags, isvd_risk_t* out) {
+  if (!h || !out || (flags & ~ISVD_RISK_FULL)) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  if (w && !w_on_device) {
+    const bool ok = h->prec == ISVD_FP64 ? host_finite((const double*)w, h->n) : host_finite((const float*)w, h->n);
+    if (!ok) return fail(h, ISVD_ENONFINITE, "non-finite portfolio weight");
+  }
+  return h->prec == ISVD_FP64 ? do_risk<double>(h, w, w_on_device, flags, out)
+                              : do_risk<float>(h, w, w_on_device, flags, out);
 }
 
 isvd_status isvd_sync(isvd_t h) {

@@ -20,20 +20,25 @@
 // dropped levels (D3, D4) and the fixed-point rounding are below 2^-24 relative to the inputs'
 // magnitudes, as for an FP32 dot product, and unbiased.
 //
-// One CTA of 128 threads handles 128 rows of one side of one update (the rotation block -> update
-// tables of the warp kernel, with 128 rows per block for these buckets):
-//   1. thread 0 starts one bulk copy (TMA) of the contiguous row tile (rows x KB FP32) into
-//      shared memory; meanwhile the CTA cuts the core factor (V_K or U_K; rows >= r and columns
-//      >= k_out zeroed) into digit planes (B operands, K-major) and per-column scales;
-//   2. each thread takes one row: z_hat = (x_row - row . p) / rho in float-float when the
-//      projection side gains the new direction, then the row's scale and digit planes (A operands);
-//   3. thread 0 issues the six digit-product MMAs per K step of 16 (M = 128, N = KB, BF16, FP32
-//      accumulation) into the three level accumulators and commits them to an mbarrier;
-//   4. each warp loads its 32 lanes of the three accumulators (one row per thread), combines them,
-//      adds z_hat times the core factor's last row, writes the row back into the staging tile, and
-//      thread 0 stores the tile with one bulk copy.
-// Every wait is bounded in wall time; on a timeout the stream's sticky status gets kStTimeout,
-// the CTA waits (bounded) for its copies, frees its TMEM and returns.
+// Work split. A rotation block is 128 rows of one side of one update (the warp kernel's block ->
+// update tables, 128 rows per block for these buckets). Persistent CTAs of 128 threads (a few per
+// SM) each take a contiguous range of blocks, so consecutive blocks mostly share their update and
+// side and the core factor's digit planes are cut once per run of blocks. Per block:
+//   1. the block's row tile (rows x KB FP32, contiguous) was brought into one of two shared-memory
+//      stages by a bulk copy (TMA) issued one block ahead; the next block's copy is issued now;
+//   2. if the update or side changed: the core factor (V_K or U_K; rows >= r and columns >= k_out
+//      zeroed) is cut into digit planes (B operands, K-major) with per-column scales, four threads
+//      per column;
+//   3. each thread takes one row: z_hat = (x_row - row . p) / rho in float-float when the projection
+//      side gains the new direction, then the row's scale and digit planes (A operands);
+//   4. thread 0 issues the six digit-product MMAs per K step of 16 (M = 128, N = KB, BF16, FP32
+//      accumulation) into the three level accumulators (TMEM, allocated once per CTA) and commits
+//      them to an mbarrier;
+//   5. each warp loads its 32 lanes of the three accumulators (one row per thread), combines them,
+//      adds z_hat times the core factor's last row, writes the row back into its stage, and thread
+//      0 starts the bulk store of the stage (waited for only before the stage is loaded again).
+// Every wait is bounded in wall time; on a timeout the stream's sticky status gets kStTimeout and
+// the CTA stops, waits (bounded) for its copies, frees its TMEM and returns.
 #pragma once
 
 #include "pool_warp.cuh"
@@ -47,18 +52,19 @@ constexpr uint64_t kTcWaitNs = 2000ull * 1000 * 1000;  // 2 s
 
 template <int KB>
 struct TcRotLayout {
-  static constexpr uint32_t kTile = kTcRotRows * KB * 4;      // FP32 staging tile
+  static constexpr uint32_t kTile = kTcRotRows * KB * 4;      // FP32 staging tile (one stage)
   static constexpr uint32_t kAplane = kTcRotRows * KB * 2;    // one BF16 digit plane of the tile
   static constexpr uint32_t kBplane = KB * KB * 2;            // one BF16 digit plane of the core factor
-  static constexpr uint32_t kOffA = kTile;                    // three A planes
+  static constexpr uint32_t kOffA = 2 * kTile;                // two stages, then three A planes
   static constexpr uint32_t kOffB = kOffA + 3 * kAplane;      // three B planes
   static constexpr uint32_t kOffVec = kOffB + 3 * kBplane;    // z row, p hi, p lo, column scales
-  static constexpr uint32_t kOffBar = kOffVec + 4 * KB * 4;   // two mbarriers
-  static constexpr uint32_t kOffTmem = kOffBar + 16;
+  static constexpr uint32_t kOffBar = kOffVec + 4 * KB * 4;   // mbarriers: two stages, MMA
+  static constexpr uint32_t kOffTmem = kOffBar + 32;
   static constexpr uint32_t kBytes = kOffTmem + 16;
   static constexpr uint32_t kTmemCols = 3 * KB <= 32 ? 32 : 3 * KB <= 64 ? 64 : 128;  // three levels
   static constexpr uint32_t kSbo = 8 * KB * 2;                // bytes per 8-row group (16-bit elements)
 };
+constexpr int kTcCtasPerSm = 3;  // persistent CTAs per SM (shared memory allows three at KB = 32)
 
 // Block fixed point: the exponent e with max |v| < 2^e (0 for an all-zero set).
 __device__ __forceinline__ int fixed_exponent(float amax) {
@@ -85,48 +91,69 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xFFFF0000u);
 }
 
+// Where rotation block b sits: its update, side, first row and row count.
+template <int KB>
+struct TcBlock {
+  int e, rows;
+  bool pside, withz;
+  int64_t base;
+  __device__ __forceinline__ void locate(const PoolOp* ops, const RotScratch<KB>* scratch, const int* chunk_start,
+                                         const int* block_op, int b) {
+    e = block_op[b];
+    const PoolOp& op = ops[e];
+    const bool is_row = op.kind == kRow;
+    const int64_t nP = is_row ? op.n : op.m, nQ = is_row ? op.m : op.n;
+    const int cP = (int)((nP + kTcRotRows - 1) / kTcRotRows);
+    const int ci = b - chunk_start[e];
+    pside = ci < cP;
+    withz = pside && scratch[e].grew;
+    const int64_t nrows = pside ? nP : nQ;
+    base = (int64_t)(pside ? ci : ci - cP) * kTcRotRows;
+    rows = (int)(nrows - base < kTcRotRows ? nrows - base : kTcRotRows);
+  }
+  __device__ __forceinline__ float* tile(const PoolOp* ops) const {
+    const PoolOp& op = ops[e];
+    const bool is_row = op.kind == kRow;
+    return (pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V)) + base * KB;
+  }
+};
+
+// First block at or after b (below b1) whose update has work (k_out >= 0), or b1.
+template <int KB>
+__device__ __forceinline__ int tc_next_live(const RotScratch<KB>* scratch, const int* block_op, int b, int b1) {
+  while (b < b1 && scratch[block_op[b]].k_out < 0) ++b;
+  return b;
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kTcRotThreads)
     k_pool_rotate_tc(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
-                     const int* __restrict__ chunk_start, const int* __restrict__ block_op) {
+                     const int* __restrict__ chunk_start, const int* __restrict__ block_op, int nblocks) {
   static_assert(KB == 16 || KB == 32, "tensor-core rotation buckets");
   using L = TcRotLayout<KB>;
   constexpr int C4 = KB / 4;  // float4 chunks per row
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* T = reinterpret_cast<float*>(smem);
+  auto stage_buf = [&](int st_) { return reinterpret_cast<float*>(smem + (uint32_t)st_ * L::kTile); };
   unsigned char* Ad = smem + L::kOffA;
   unsigned char* Bd = smem + L::kOffB;
   float* zrow = reinterpret_cast<float*>(smem + L::kOffVec);
   float* ph = zrow + KB;
   float* pl = ph + KB;
   float* bscale = pl + KB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kOffBar);  // tile landed in stage 0 / 1
+  uint64_t* mmab = full + 2;                                          // MMAs of a block completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmem);
-
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int e = block_op[blockIdx.x];
-  const RotScratch<KB>& sc = scratch[e];
-  const int k_out = sc.k_out;
-  if (k_out < 0) return;  // handed to the CTA kernel (uniform over the block)
-  const PoolOp& op = ops[e];
-  const bool is_row = op.kind == kRow;
-  const int64_t nP = is_row ? op.n : op.m;
-  const int64_t nQ = is_row ? op.m : op.n;
-  const int cP = (int)((nP + kTcRotRows - 1) / kTcRotRows);
-  const int ci = blockIdx.x - chunk_start[e];
-  const bool pside = ci < cP;
-  const int r = sc.r;
-  const bool withz = pside && sc.grew;
-  const int64_t nrows = pside ? nP : nQ;
-  const int64_t base = (int64_t)(pside ? ci : ci - cP) * kTcRotRows;
-  const int rows = (int)(nrows - base < kTcRotRows ? nrows - base : kTcRotRows);
-  float* X = (pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V)) + base * KB;
-  const float* src = pside ? sc.RP : sc.RQ;
-  const uint32_t tile_bytes = (uint32_t)rows * KB * 4;
+
+  const int per = (nblocks + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b1 = min(nblocks, ((int)blockIdx.x + 1) * per);
+  int cur = tc_next_live<KB>(scratch, block_op, (int)blockIdx.x * per, b1);
+  if (cur >= b1) return;  // uniform: nothing to rotate in this range
 
   if (tid == 0) {
-    tc::mbar_init(&bars[0], 1);
-    tc::mbar_init(&bars[1], 1);
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_init(mmab, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, L::kTmemCols);
@@ -134,208 +161,253 @@ __global__ void __launch_bounds__(kTcRotThreads)
   __syncthreads();
   tc::tc_fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+
+  TcBlock<KB> blk;
+  blk.locate(ops, scratch, chunk_start, block_op, cur);
+  uint32_t use0 = 0u, use1 = 0u;              // completed loads per stage (mbarrier parity)
+  bool inflight0 = false, inflight1 = false;  // a load issued into the stage and not yet waited for
+  uint32_t mma_uses = 0;
+  bool mma_inflight = false;
   if (tid == 0) {
-    tc::mbar_arrive_expect_tx(&bars[0], tile_bytes);
-    tc::bulk_g2s(T, X, tile_bytes, &bars[0]);
+    tc::mbar_arrive_expect_tx(&full[0], (uint32_t)blk.rows * KB * 4);
+    tc::bulk_g2s(stage_buf(0), blk.tile(ops), (uint32_t)blk.rows * KB * 4, &full[0]);
   }
-  // Step 1: the core factor's digit planes, B[n = jj][kk = c] from R[c][jj] (c < r, jj < k_out),
-  // one output column per thread, with its own exponent.
-  if (tid < KB) {
-    const int jj = tid;
-    float amax = 0.f;
-    for (int c = 0; c < r; ++c) amax = fmaxf(amax, jj < k_out ? fabsf(src[c * KB + jj]) : 0.f);
-    const int eb = fixed_exponent(amax);
-    bscale[jj] = ldexpf(1.f, eb - 8);
-    for (int c = 0; c < KB; ++c) {
-      const float v = (c < r && jj < k_out) ? src[c * KB + jj] : 0.f;
-      float d0, d1, d2;
-      digits3(v, eb, d0, d1, d2);
-      const uint32_t o = tc::kmajor_offset16(jj, c, KB);
-      *reinterpret_cast<uint16_t*>(Bd + o) = (uint16_t)(__float_as_uint(d0) >> 16);
-      *reinterpret_cast<uint16_t*>(Bd + L::kBplane + o) = (uint16_t)(__float_as_uint(d1) >> 16);
-      *reinterpret_cast<uint16_t*>(Bd + 2 * L::kBplane + o) = (uint16_t)(__float_as_uint(d2) >> 16);
-    }
-  } else if (withz && tid < 2 * KB) {
-    const int c = tid - KB;
-    zrow[c] = c < k_out ? src[r * KB + c] : 0.f;
-    ph[c] = c < r ? sc.ph[c] : 0.f;
-    pl[c] = c < r ? sc.pl[c] : 0.f;
-  }
-  const bool got = tc::mbar_wait_bounded(&bars[0], 0, kTcWaitNs);
-  const int late = __syncthreads_or(!got);  // also: B planes, scales, z row and p complete
-  if (late) {
-    if (tid == 0) {
-      atomicOr(&op.st->status, kStTimeout);
-      tc::mbar_wait_bounded(&bars[0], 0, kTcWaitNs);  // let the copy in flight finish
-    }
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
-    return;
-  }
-
-  // Step 2: this thread's row (columns >= r are stale and count as zero).
-  const int row = tid;
-  const bool live = row < rows;
-  const float4* T4 = reinterpret_cast<const float4*>(T);
-  float xv[KB];
-#pragma unroll
-  for (int q = 0; q < C4; ++q) {
-    // chunk (q + row) mod C4 first: conflict-free across the warp; registers stay static-indexed
-    // because the chunk order is undone below with a barrel shift
-    const int qq = (q + row) % C4;
-    const float4 a = live ? T4[row * C4 + qq] : make_float4(0.f, 0.f, 0.f, 0.f);
-    xv[4 * q] = a.x;
-    xv[4 * q + 1] = a.y;
-    xv[4 * q + 2] = a.z;
-    xv[4 * q + 3] = a.w;
-  }
-  {
-    // undo the rotation: xv chunk q holds row chunk (q + sh) mod C4
-    const int sh = row % C4;
-#pragma unroll
-    for (int b = 1; b < C4; b <<= 1) {
-      if (sh & b) {
-        float tmp[KB];
-#pragma unroll
-        for (int i = 0; i < KB; ++i) tmp[i] = xv[(i - 4 * b + KB) % KB];
-#pragma unroll
-        for (int i = 0; i < KB; ++i) xv[i] = tmp[i];
+  inflight0 = true;
+  int stage = 0, prev_e = -1;
+  bool prev_side = false, failed = false;
+  while (cur < b1) {
+    const int nxt = tc_next_live<KB>(scratch, block_op, cur + 1, b1);
+    TcBlock<KB> nb;
+    if (nxt < b1) {
+      nb.locate(ops, scratch, chunk_start, block_op, nxt);
+      if (tid == 0) {
+        tc::bulk_wait_read_all();  // the other stage's last store has been read out of shared memory
+        tc::mbar_arrive_expect_tx(&full[stage ^ 1], (uint32_t)nb.rows * KB * 4);
+        tc::bulk_g2s(stage_buf(stage ^ 1), nb.tile(ops), (uint32_t)nb.rows * KB * 4, &full[stage ^ 1]);
       }
+      if (stage) inflight0 = true;
+      else inflight1 = true;
     }
-  }
-  float amax = 0.f;
+    const RotScratch<KB>& sc = scratch[blk.e];
+    const PoolOp& op = ops[blk.e];
+    const int r = sc.r, k_out = sc.k_out;
+    if (blk.e != prev_e || blk.pside != prev_side) {
+      // The core factor's digit planes, B[n = jj][kk = c] from R[c][jj] (c < r, jj < k_out), four
+      // threads per output column jj (rows split four ways), the column's exponent by shuffles.
+      // The previous block's MMAs, the last readers of these planes, have completed.
+      const float* src = blk.pside ? sc.RP : sc.RQ;
+      constexpr int RPT = KB / 4;
+      if (tid < 4 * KB) {
+        const int jj = tid >> 2, sub = tid & 3;
+        float v[RPT];
+        float amax = 0.f;
 #pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    if (c >= r) xv[c] = 0.f;
-    amax = fmaxf(amax, fabsf(xv[c]));
-  }
-  float zh = 0.f;
-  if (withz && live) {
-    ff s{op.x[base + row], 0.f};
+        for (int q = 0; q < RPT; ++q) {
+          const int c = sub * RPT + q;
+          v[q] = (c < r && jj < k_out) ? src[c * KB + jj] : 0.f;
+          amax = fmaxf(amax, fabsf(v[q]));
+        }
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 2));
+        const int eb = fixed_exponent(amax);
+        if (sub == 0) bscale[jj] = ldexpf(1.f, eb - 8);
 #pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      if (c < r) {
-        ff pr = two_prod(xv[c], ph[c]);
-        pr.lo = fmaf(xv[c], pl[c], pr.lo);
-        s = ff_add(s, ff{-pr.hi, -pr.lo});
+        for (int q = 0; q < RPT; ++q) {
+          float d0, d1, d2;
+          digits3(v[q], eb, d0, d1, d2);
+          const uint32_t o = tc::kmajor_offset16(jj, sub * RPT + q, KB);
+          *reinterpret_cast<uint16_t*>(Bd + o) = (uint16_t)(__float_as_uint(d0) >> 16);
+          *reinterpret_cast<uint16_t*>(Bd + L::kBplane + o) = (uint16_t)(__float_as_uint(d1) >> 16);
+          *reinterpret_cast<uint16_t*>(Bd + 2 * L::kBplane + o) = (uint16_t)(__float_as_uint(d2) >> 16);
+        }
       }
-    }
-    zh = (s.hi + s.lo) * sc.inv_rho;
-  }
-  const int ea = fixed_exponent(amax);
-  const float ascale = ldexpf(1.f, ea - 8);
-#pragma unroll
-  for (int g = 0; g < KB / 8; ++g) {  // one 16-byte core-matrix row per digit plane
-    uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      float a0, a1, a2, b0, b1, b2;
-      digits3(xv[8 * g + 2 * h], ea, a0, a1, a2);
-      digits3(xv[8 * g + 2 * h + 1], ea, b0, b1, b2);
-      w0[h] = pack_bf16x2(a0, b0);
-      w1[h] = pack_bf16x2(a1, b1);
-      w2[h] = pack_bf16x2(a2, b2);
-    }
-    const uint32_t o = tc::kmajor_offset16(row, 8 * g, KB);
-    *reinterpret_cast<uint4*>(Ad + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    *reinterpret_cast<uint4*>(Ad + L::kAplane + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4*>(Ad + 2 * L::kAplane + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-  }
-  tc::fence_proxy_async_smem();
-  __syncthreads();
-
-  // Step 3: level l accumulator at TMEM columns l * KB; per K step of 16 the digit pairs (i, j)
-  // with i + j = l.
-  if (tid == 0) {
-    tc::tc_fence_after_sync();
-    constexpr uint32_t idesc = tc::idesc_bf16(128, KB);
-    const uint32_t a0 = tc::smem_u32(Ad), b0 = tc::smem_u32(Bd);
-#pragma unroll
-    for (int s = 0; s < KB / 16; ++s) {
-      const uint32_t ko = (uint32_t)s * 256u;  // two core matrices along K
-      uint64_t da[3], db[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        da[i] = tc::smem_desc_kmajor(a0 + i * L::kAplane + ko, 128, L::kSbo);
-        db[i] = tc::smem_desc_kmajor(b0 + i * L::kBplane + ko, 128, L::kSbo);
+      if (tid < KB) {
+        zrow[tid] = (blk.pside && tid < k_out) ? src[r * KB + tid] : 0.f;
+        ph[tid] = tid < r ? sc.ph[tid] : 0.f;
+        pl[tid] = tid < r ? sc.pl[tid] : 0.f;
       }
-      const uint32_t acc = s > 0 ? 1u : 0u;
-      tc::mma_bf16(tmem, da[0], db[0], idesc, acc);
-      tc::mma_bf16(tmem + KB, da[0], db[1], idesc, acc);
-      tc::mma_bf16(tmem + KB, da[1], db[0], idesc, 1u);
-      tc::mma_bf16(tmem + 2 * KB, da[0], db[2], idesc, acc);
-      tc::mma_bf16(tmem + 2 * KB, da[1], db[1], idesc, 1u);
-      tc::mma_bf16(tmem + 2 * KB, da[2], db[0], idesc, 1u);
+      prev_e = blk.e;
+      prev_side = blk.pside;
     }
-    tc::mma_commit(&bars[1]);
-  }
-  const bool done = tc::mbar_wait_bounded(&bars[1], 0, kTcWaitNs);
-  const int late2 = __syncthreads_or(!done);
-  if (late2) {
-    if (tid == 0) {
-      atomicOr(&op.st->status, kStTimeout);
-      tc::mbar_wait_bounded(&bars[1], 0, kTcWaitNs);
+    const bool got = tc::mbar_wait_bounded(&full[stage], (stage ? use1 : use0) & 1u, kTcWaitNs);
+    if (__syncthreads_or(!got)) {  // also: the B planes, scales, z row and p are complete
+      failed = true;
+      break;
     }
-    tc::tc_fence_before_sync();
-    __syncthreads();
-    if (warp == 0) {
-      tc::tc_fence_after_sync();
-      tc::tmem_dealloc(tmem, L::kTmemCols);
-    }
-    return;
-  }
-  tc::tc_fence_after_sync();
-
-  // Step 4: warp w reads TMEM lanes 32 w .. 32 w + 31, i.e. rows 32 w .. 32 w + 31 of the tile.
-  {
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
-    float acc[KB], lv[KB];
-    if constexpr (KB == 32) {
-      tc::tmem_ld32(lane_addr + 2 * KB, acc);
-      tc::tmem_ld32(lane_addr + KB, lv);
+    if (stage) {
+      use1++;
+      inflight1 = false;
     } else {
-      tc::tmem_ld16(lane_addr + 2 * KB, acc);
-      tc::tmem_ld16(lane_addr + KB, lv);
+      use0++;
+      inflight0 = false;
     }
+
+    // This thread's row (columns >= r are stale and count as zero).
+    float* T = stage_buf(stage);
+    const int row = tid;
+    const bool live = row < blk.rows;
+    const float4* T4 = reinterpret_cast<const float4*>(T);
+    float xv[KB];
 #pragma unroll
-    // D1 + D2 / 2^8, rounded once: that rounding is scaled down by 2^-8 in the result below
-    for (int j = 0; j < KB; ++j) acc[j] = fmaf(acc[j], 1.f / 256.f, lv[j]);
-    if constexpr (KB == 32) tc::tmem_ld32(lane_addr, lv);
-    else tc::tmem_ld16(lane_addr, lv);
-#pragma unroll
-    for (int j = 0; j < KB; ++j) {
-      float y = fmaf(acc[j], 1.f / 256.f, lv[j]) * (ascale * bscale[j]);
-      if (withz) y = fmaf(zh, zrow[j], y);
-      acc[j] = y;
+    for (int q = 0; q < C4; ++q) {
+      // chunk (q + row) mod C4 first: conflict-free across the warp; the chunk order is undone by a
+      // barrel shift so that register indices stay static
+      const int qq = (q + row) % C4;
+      const float4 a = live ? T4[row * C4 + qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[4 * q] = a.x;
+      xv[4 * q + 1] = a.y;
+      xv[4 * q + 2] = a.z;
+      xv[4 * q + 3] = a.w;
     }
-    if (live) {
-      // Write step q stores chunk (q + row) mod C4 (conflict-free across the warp); rotate the
-      // registers first so that every register index is static.
+    {
       const int sh = row % C4;
 #pragma unroll
       for (int b = 1; b < C4; b <<= 1) {
         if (sh & b) {
           float tmp[KB];
 #pragma unroll
-          for (int i = 0; i < KB; ++i) tmp[i] = acc[(i + 4 * b) % KB];
+          for (int i = 0; i < KB; ++i) tmp[i] = xv[(i - 4 * b + KB) % KB];
 #pragma unroll
-          for (int i = 0; i < KB; ++i) acc[i] = tmp[i];
+          for (int i = 0; i < KB; ++i) xv[i] = tmp[i];
         }
       }
-      float4* W4 = reinterpret_cast<float4*>(T);
-#pragma unroll
-      for (int q = 0; q < C4; ++q)
-        W4[row * C4 + (q + sh) % C4] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
+    float amax = 0.f;
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c >= r) xv[c] = 0.f;
+      amax = fmaxf(amax, fabsf(xv[c]));
+    }
+    float zh = 0.f;
+    if (blk.withz && live) {
+      ff sacc{op.x[blk.base + row], 0.f};
+#pragma unroll
+      for (int c = 0; c < KB; ++c) {
+        if (c < r) {
+          ff pr = two_prod(xv[c], ph[c]);
+          pr.lo = fmaf(xv[c], pl[c], pr.lo);
+          sacc = ff_add(sacc, ff{-pr.hi, -pr.lo});
+        }
+      }
+      zh = (sacc.hi + sacc.lo) * sc.inv_rho;
+    }
+    const int ea = fixed_exponent(amax);
+    const float ascale = ldexpf(1.f, ea - 8);
+#pragma unroll
+    for (int g = 0; g < KB / 8; ++g) {  // one 16-byte core-matrix row per digit plane
+      uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float a0, a1, a2, c0, c1, c2;
+        digits3(xv[8 * g + 2 * h], ea, a0, a1, a2);
+        digits3(xv[8 * g + 2 * h + 1], ea, c0, c1, c2);
+        w0[h] = pack_bf16x2(a0, c0);
+        w1[h] = pack_bf16x2(a1, c1);
+        w2[h] = pack_bf16x2(a2, c2);
+      }
+      const uint32_t o = tc::kmajor_offset16(row, 8 * g, KB);
+      *reinterpret_cast<uint4*>(Ad + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+      *reinterpret_cast<uint4*>(Ad + L::kAplane + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+      *reinterpret_cast<uint4*>(Ad + 2 * L::kAplane + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+
+    // Level l accumulator at TMEM columns l * KB; per K step of 16 the digit pairs (i, j), i + j = l.
+    if (tid == 0) {
+      tc::tc_fence_after_sync();
+      constexpr uint32_t idesc = tc::idesc_bf16(128, KB);
+      const uint32_t a0 = tc::smem_u32(Ad), bb0 = tc::smem_u32(Bd);
+#pragma unroll
+      for (int sk = 0; sk < KB / 16; ++sk) {
+        const uint32_t ko = (uint32_t)sk * 256u;  // two core matrices along K
+        uint64_t da[3], db[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          da[i] = tc::smem_desc_kmajor(a0 + i * L::kAplane + ko, 128, L::kSbo);
+          db[i] = tc::smem_desc_kmajor(bb0 + i * L::kBplane + ko, 128, L::kSbo);
+        }
+        const uint32_t acc = sk > 0 ? 1u : 0u;
+        tc::mma_bf16(tmem, da[0], db[0], idesc, acc);
+        tc::mma_bf16(tmem + KB, da[0], db[1], idesc, acc);
+        tc::mma_bf16(tmem + KB, da[1], db[0], idesc, 1u);
+        tc::mma_bf16(tmem + 2 * KB, da[0], db[2], idesc, acc);
+        tc::mma_bf16(tmem + 2 * KB, da[1], db[1], idesc, 1u);
+        tc::mma_bf16(tmem + 2 * KB, da[2], db[0], idesc, 1u);
+      }
+      tc::mma_commit(mmab);
+    }
+    mma_inflight = true;
+    const bool done = tc::mbar_wait_bounded(mmab, mma_uses & 1u, kTcWaitNs);
+    if (__syncthreads_or(!done)) {
+      failed = true;
+      break;
+    }
+    mma_uses++;
+    mma_inflight = false;
+    tc::tc_fence_after_sync();
+
+    // Warp w reads TMEM lanes 32 w .. 32 w + 31: rows 32 w .. 32 w + 31 of the tile, its own rows.
+    {
+      const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+      float acc[KB], lv[KB];
+      if constexpr (KB == 32) {
+        tc::tmem_ld32(lane_addr + 2 * KB, acc);
+        tc::tmem_ld32(lane_addr + KB, lv);
+      } else {
+        tc::tmem_ld16(lane_addr + 2 * KB, acc);
+        tc::tmem_ld16(lane_addr + KB, lv);
+      }
+      // D1 + D2 / 2^8, rounded once: that rounding is scaled down by 2^-8 in the result below
+#pragma unroll
+      for (int j = 0; j < KB; ++j) acc[j] = fmaf(acc[j], 1.f / 256.f, lv[j]);
+      if constexpr (KB == 32) tc::tmem_ld32(lane_addr, lv);
+      else tc::tmem_ld16(lane_addr, lv);
+#pragma unroll
+      for (int j = 0; j < KB; ++j) {
+        float y = fmaf(acc[j], 1.f / 256.f, lv[j]) * (ascale * bscale[j]);
+        if (blk.withz) y = fmaf(zh, zrow[j], y);
+        acc[j] = y;
+      }
+      if (live) {
+        const int sh = row % C4;
+#pragma unroll
+        for (int b = 1; b < C4; b <<= 1) {
+          if (sh & b) {
+            float tmp[KB];
+#pragma unroll
+            for (int i = 0; i < KB; ++i) tmp[i] = acc[(i + 4 * b) % KB];
+#pragma unroll
+            for (int i = 0; i < KB; ++i) acc[i] = tmp[i];
+          }
+        }
+        float4* W4 = reinterpret_cast<float4*>(T);
+#pragma unroll
+        for (int q = 0; q < C4; ++q)
+          W4[row * C4 + (q + sh) % C4] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before_sync();
+    __syncthreads();  // the tile is complete, and every warp is done with the accumulators
+    if (tid == 0) {
+      tc::bulk_s2g(blk.tile(ops), T, (uint32_t)blk.rows * KB * 4);
+      tc::bulk_commit();
+    }
+    stage ^= 1;
+    cur = nxt;
+    if (cur < b1) blk = nb;
   }
-  tc::fence_proxy_async_smem();
+  if (failed && tid == 0) {
+    atomicOr(&ops[blk.e].st->status, kStTimeout);
+    // let the copies and MMAs in flight finish (bounded) before the CTA's memory goes away
+    if (inflight0) tc::mbar_wait_bounded(&full[0], use0 & 1u, kTcWaitNs);
+    if (inflight1) tc::mbar_wait_bounded(&full[1], use1 & 1u, kTcWaitNs);
+    if (mma_inflight) tc::mbar_wait_bounded(mmab, mma_uses & 1u, kTcWaitNs);
+  }
+  if (tid == 0) tc::bulk_wait_all();
   tc::tc_fence_before_sync();
   __syncthreads();
-  if (tid == 0) {
-    tc::bulk_s2g(X, T, tile_bytes);
-    tc::bulk_commit();
-    tc::bulk_wait_all();
-  }
   if (warp == 0) {
     tc::tc_fence_after_sync();
     tc::tmem_dealloc(tmem, L::kTmemCols);

@@ -1,5 +1,7 @@
 // Pool warp-per-update kernels (projection + core of one append per warp) and the row-parallel
 // rotation kernels they feed, for rank buckets 8, 16 and 32.
+#include <algorithm>
+
 #include "launch.cuh"
 #include "pool_reorth.cuh"
 #include "pool_rotate_tc.cuh"
@@ -21,11 +23,23 @@ void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* s
   k_pool_rotate<KB><<<nblocks, kPoolRotThreads, rot_smem_bytes<KB>(), s>>>(
       ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op);
 }
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+  }
+  return sms;
+}
 template <int KB>
 void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
                       const int* block_op) {
-  k_pool_rotate_tc<KB><<<nblocks, kTcRotThreads, TcRotLayout<KB>::kBytes, s>>>(
-      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op);
+  // Persistent CTAs: a few per SM, each over a contiguous range of the rotation blocks.
+  const int grid = std::min(nblocks, kTcCtasPerSm * device_sms());
+  if (grid <= 0) return;
+  k_pool_rotate_tc<KB><<<grid, kTcRotThreads, TcRotLayout<KB>::kBytes, s>>>(
+      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks);
 }
 }  // namespace
 

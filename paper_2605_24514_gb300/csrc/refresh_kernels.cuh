@@ -338,6 +338,62 @@ __global__ void k_chol_rinv(const double* __restrict__ B, int r, double* __restr
   if (threadIdx.x == 0) *info = bad;
 }
 
+// Portfolio risk and covariance error from r x r Gram matrices (Section 5.3): g = V^T w,
+// G1 = V^T V, and for the optimal factors gopt, G2 = Vopt^T Vopt, C = V^T Vopt. With
+// S = V diag(s^2) V^T, w^T S w = sum_i s_i^2 g_i^2 and ||S1 - S2||_F^2 = sum s1_i^2 s1_j^2 G1_ij^2 +
+// sum s2_i^2 s2_j^2 G2_ij^2 - 2 sum s1_i^2 s2_j^2 C_ij^2 (no orthonormality assumed). out = {vol,
+// vol_opt, risk_error, cov_error, cov_norm}.
+static __global__ void k_risk_finish(const double* __restrict__ s1, const double* __restrict__ s2,
+                                     const double* __restrict__ g, const double* __restrict__ gopt,
+                                     const double* __restrict__ G1, const double* __restrict__ G2,
+                                     const double* __restrict__ Cx, int r, double inv_t1, int full,
+                                     double* __restrict__ out) {
+  __shared__ double red[5][8];
+  double a = 0.0, b = 0.0, x = 0.0, v1 = 0.0, v2 = 0.0;
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    const int i = idx / r, j = idx - i * r;
+    const double q1 = s1[i] * s1[i] * s1[j] * s1[j];
+    a += q1 * G1[idx] * G1[idx];
+    if (full) {
+      b += s2[i] * s2[i] * s2[j] * s2[j] * G2[idx] * G2[idx];
+      x += s1[i] * s1[i] * s2[j] * s2[j] * Cx[idx] * Cx[idx];
+    }
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    v1 += s1[i] * s1[i] * g[i] * g[i];
+    if (full) v2 += s2[i] * s2[i] * gopt[i] * gopt[i];
+  }
+  double vals[5] = {a, b, x, v1, v2};
+  for (int q = 0; q < 5; ++q) {
+    double v = vals[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < 5; ++q)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[q] += red[q][w];
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    out[0] = sqrt(fmax(t[3], 0.0) * inv_t1);
+    out[4] = sqrt(fmax(t[0], 0.0)) * inv_t1;
+    if (full) {
+      out[1] = sqrt(fmax(t[4], 0.0) * inv_t1);
+      out[2] = fabs(out[0] - out[1]) / out[1];
+      out[3] = sqrt(fmax(t[0] + t[1] - 2.0 * t[2], 0.0) / t[1]);
+    } else {
+      out[1] = out[2] = out[3] = nan;
+    }
+  }
+}
+
+// v[i] = value, i < n.
+template <typename T>
+__global__ void k_fill(T* __restrict__ v, int64_t n, T value) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = value;
+}
+
 }  // namespace isvd
 
 namespace isvd {
