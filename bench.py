@@ -460,13 +460,21 @@ def run_batched(args):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        pool.profile(True)                          # host phase times of the e2e submits
         t0 = time.perf_counter()
         n_rec = 0
+        t_sub = t_gat = t_pol = 0.0
         for q in range(K):
             seg = pinned[q * tick_len:(q + 1) * tick_len]
+            a = time.perf_counter()
             pool.submit_raw(ops, S, seg.data_ptr(), tick_len, 0)
+            b_ = time.perf_counter()
             pool.gather_sigma(32, out=sig_out[q % 2].numpy())
+            c_ = time.perf_counter()
             n_rec += pool.poll().size
+            t_sub += b_ - a
+            t_gat += c_ - b_
+            t_pol += time.perf_counter() - c_
         pool.sync()
         while True:
             got = pool.poll().size
@@ -475,10 +483,15 @@ def run_batched(args):
             n_rec += got
         el = reduce_max(time.perf_counter() - t0, world)
         assert n_rec == K * S, (n_rec, K * S)
+        e2e_phases, _ = pool.host_profile()
+        pool.profile(False)
         d2h = pool.slots * 32 * 8 + S * 48
         e2e = {"value": world * K * S / el, "unit": "updates/s",
                "h2d_bytes_per_step": int(tick_len * 4 + S * 136), "d2h_bytes_per_step": int(d2h),
-               "results": "all streams' sigma (gather, one D2H copy) and one completion record per update, per tick"}
+               "results": "all streams' sigma (gather, one D2H copy) and one completion record per update, per tick",
+               "host_us_per_step": {"submit": round(1e6 * t_sub / K, 1), "gather": round(1e6 * t_gat / K, 1),
+                                    "poll": round(1e6 * t_pol / K, 1),
+                                    "submit_phases": {k: round(v / K, 1) for k, v in e2e_phases.items()}}}
     # Error ratio (Section 2.5) of a sample of streams after all ticks; the CPU-baseline leg replays
     # the same streams through the oracle and compares.
     sample_ids = list(range(min(S, args.acc_streams)))

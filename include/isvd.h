@@ -264,8 +264,8 @@ typedef struct {
 
 /* isvd_pool_config.flags */
 #define ISVD_POOL_SIMT_ROTATIONS 1  /* rotate on the FP32 pipes in every rank bucket (default: the
-                                       tensor-core rotation with split-TF32 operands for buckets 16
-                                       and 32) */
+                                       tensor-core rotation with exact BF16 digit products for
+                                       buckets 16 and 32) */
 #define ISVD_POOL_COMPLETIONS 2     /* every op of a submit leaves a completion record for
                                        isvd_pool_poll */
 

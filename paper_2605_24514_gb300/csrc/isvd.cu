@@ -14,6 +14,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/isvd.h"
 #include "launch.cuh"
 #include "pool_kernels.cuh"
@@ -1471,6 +1473,11 @@ struct isvd_pool_ctx {
   DevState* zero_st = nullptr;
   double* gather_dev = nullptr;
   int64_t gather_cap = 0;
+  // Tensor maps (CUtensorMap, 128 bytes) of every slot's U and V for the tensor-core rotations
+  // (TMA loads of 128-row boxes, swizzled), rebuilt when a stream's U or V is reallocated.
+  CUtensorMap* tmaps_dev = nullptr;
+  int64_t tmaps_cap = 0;  // slots
+  std::vector<const void*> tmap_u, tmap_v;  // the base addresses the maps were built for
   int64_t reorth_cap = 0;
   int64_t reorth_runs = 0;
   // Streams whose monitor is due; checked together once a full wave of them has gathered (or one
@@ -1609,7 +1616,8 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
                                const int* block_op, int nblocks) {
   const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
-  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, !(p->flags & ISVD_POOL_SIMT_ROTATIONS));
+  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, !(p->flags & ISVD_POOL_SIMT_ROTATIONS),
+                                     p->tmaps_dev);
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1657,6 +1665,71 @@ isvd_status pool_set_slot(isvd_pool_ctx* p, int64_t id, const double* sig, const
       cudaMemcpyAsync(p->tab_st + id, &st, sizeof(void*), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
       cudaStreamSynchronize(p->stream) != cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool slot tables");
+  return ISVD_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time dependency).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// A map over a rows x ld FP32 matrix (row-major) with 128-row boxes of the full row width: 128-byte
+// swizzle for 128-byte rows, 64-byte swizzle for 64-byte rows (the widths the tensor-core rotation
+// serves); zeroed for other widths (never used). Rows beyond `rows` read as zeros.
+bool encode_rows_map(CUtensorMap* m, const void* base, int64_t rows, int ld) {
+  memset(m, 0, sizeof(*m));
+  if (ld != 16 && ld != 32) return true;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)ld, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUtensorMapSwizzle sw = ld == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// (Re)builds slot id's two maps if its U or V moved; the pool's stream must be idle for this slot
+// (admission, or right after a reallocation, which synchronises).
+isvd_status pool_set_maps(isvd_pool_ctx* p, int64_t id, const isvd_ctx* h) {
+  if (id >= p->tmaps_cap) {
+    const int64_t cap = std::max<int64_t>(id + 1, 2 * p->tmaps_cap);
+    CUtensorMap* d = nullptr;
+    if (cudaMalloc((void**)&d, sizeof(CUtensorMap) * 2 * (size_t)cap) != cudaSuccess)
+      return pool_fail(p, ISVD_ENOMEM, "pool tensor maps");
+    cudaStreamSynchronize(p->stream);
+    if (p->tmaps_dev) {
+      cudaMemcpy(d, p->tmaps_dev, sizeof(CUtensorMap) * 2 * (size_t)p->tmaps_cap, cudaMemcpyDeviceToDevice);
+      cudaFree(p->tmaps_dev);
+    }
+    p->tmaps_dev = d;
+    p->tmaps_cap = cap;
+    p->tmap_u.resize(cap, nullptr);
+    p->tmap_v.resize(cap, nullptr);
+  }
+  if (p->tmap_u[id] == h->U && p->tmap_v[id] == h->V) return ISVD_OK;
+  CUtensorMap m[2];
+  if (!encode_rows_map(&m[0], h->U, h->row_cap, h->ld) || !encode_rows_map(&m[1], h->V, h->col_cap, h->ld))
+    return pool_fail(p, ISVD_ECUDA, "cuTensorMapEncodeTiled failed");
+  if (cudaMemcpy(p->tmaps_dev + 2 * id, m, sizeof m, cudaMemcpyHostToDevice) != cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool tensor map copy");
+  p->tmap_u[id] = h->U;
+  p->tmap_v[id] = h->V;
   return ISVD_OK;
 }
 
@@ -1757,6 +1830,7 @@ void isvd_pool_destroy(isvd_pool_t p) {
   if (p->zero_sig) cudaFree(p->zero_sig);
   if (p->zero_st) cudaFree(p->zero_st);
   if (p->gather_dev) cudaFree(p->gather_dev);
+  if (p->tmaps_dev) cudaFree(p->tmaps_dev);
   for (auto& sg : p->stage) {
     if (sg.ops) cudaFreeHost(sg.ops);
     if (sg.chunks) cudaFreeHost(sg.chunks);
@@ -1809,6 +1883,7 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   h->orth_on_device = 1;
   h->since_orth = p->orth_every > 0 ? ((int64_t)id * 37) % p->orth_every : 0;
   if ((s = pool_set_slot(p, id, h->sig, h->st))) return s;
+  if ((s = pool_set_maps(p, id, h))) return s;
   if (p->s_gen.size() < p->streams.size()) {
     const size_t ns = p->streams.size();
     p->s_m.resize(ns);
@@ -1830,6 +1905,7 @@ isvd_status isvd_pool_release(isvd_pool_t p, int32_t sid) {
   isvd_destroy(p->streams[sid]);
   p->streams[sid] = nullptr;
   pool_set_slot(p, sid, p->zero_sig, p->zero_st);
+  if (sid < (int64_t)p->tmap_u.size()) p->tmap_u[sid] = p->tmap_v[sid] = nullptr;
   if (sid < (int32_t)p->reorth_due_t.size() && p->reorth_due_t[sid] >= 0) {
     p->reorth_due_t[sid] = -1;
     p->reorth_pending.erase(std::find(p->reorth_pending.begin(), p->reorth_pending.end(), sid));
@@ -2066,6 +2142,8 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     isvd_ctx* h = p->streams[sid];
     if ((s = ensure_rows(h, mm[sid] + 1))) return s;
     if ((s = ensure_cols(h, nn[sid] + 1))) return s;
+    // a reallocation moved U or V (and synchronised the stream): rebuild the slot's maps
+    if ((p->tmap_u[sid] != h->U || p->tmap_v[sid] != h->V) && (s = pool_set_maps(p, sid, h))) return s;
   }
   std::vector<char>& fused = p->v_fused;
   fused.assign(nops, 0);

@@ -38,9 +38,10 @@ cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* op
                              void* scratch, const int* chunks, int* block_op, int rot_rows);
 // Rows of one side per rotation block for rank bucket kb (the warp kernel's block tables).
 int pool_rot_rows(int kb, bool use_tc);
-// use_tc selects the tensor-core rotation (k_pool_rotate_tc, buckets 16 and 32).
+// use_tc selects the tensor-core rotation (k_pool_rotate_tc, buckets 16 and 32), which loads its row
+// tiles through the pool's tensor maps (two per stream slot: U, V).
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
-                               const int* chunks, const int* block_op, bool use_tc);
+                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps);
 cudaError_t pool_warp_set_attrs();
 
 // Batched loss-of-orthogonality monitor / re-orthogonalisation (k_pool_reorth), one CTA per

@@ -24,8 +24,10 @@
 // update tables, 128 rows per block for these buckets). Persistent CTAs of 128 threads (a few per
 // SM) each take a contiguous range of blocks, so consecutive blocks mostly share their update and
 // side and the core factor's digit planes are cut once per run of blocks. Per block:
-//   1. the block's row tile (rows x KB FP32, contiguous) was brought into one of two shared-memory
-//      stages by a bulk copy (TMA) issued one block ahead; the next block's copy is issued now;
+//   1. the block's row tile (a 128-row box of the stream's U or V, through the pool's tensor map
+//      of that matrix: a TMA load, swizzled so that a thread reading its row meets no bank
+//      conflicts, rows past the matrix read as zeros) was brought into one of two shared-memory
+//      stages one block ahead; the next block's load is issued now;
 //   2. if the update or side changed: the core factor (V_K or U_K; rows >= r and columns >= k_out
 //      zeroed) is cut into digit planes (B operands, K-major) with per-column scales, four threads
 //      per column;
@@ -35,8 +37,8 @@
 //      accumulation) into the three level accumulators (TMEM, allocated once per CTA) and commits
 //      them to an mbarrier;
 //   5. each warp loads its 32 lanes of the three accumulators (one row per thread), combines them,
-//      adds z_hat times the core factor's last row, writes the row back into its stage, and thread
-//      0 starts the bulk store of the stage (waited for only before the stage is loaded again).
+//      adds z_hat times the core factor's last row, and stores the row to global memory (a warp's
+//      stores fill its 32 rows' lines).
 // Every wait is bounded in wall time; on a timeout the stream's sticky status gets kStTimeout and
 // the CTA stops, waits (bounded) for its copies, frees its TMEM and returns.
 #pragma once
@@ -60,35 +62,59 @@ struct TcRotLayout {
   static constexpr uint32_t kOffVec = kOffB + 3 * kBplane;    // z row, p hi, p lo, column scales
   static constexpr uint32_t kOffBar = kOffVec + 4 * KB * 4;   // mbarriers: two stages, MMA
   static constexpr uint32_t kOffTmem = kOffBar + 32;
-  static constexpr uint32_t kBytes = kOffTmem + 16;
+  static constexpr uint32_t kBytes = kOffTmem + 16 + 1024;  // + room to align the base to 1 KiB
   static constexpr uint32_t kTmemCols = 3 * KB <= 32 ? 32 : 3 * KB <= 64 ? 64 : 128;  // three levels
   static constexpr uint32_t kSbo = 8 * KB * 2;                // bytes per 8-row group (16-bit elements)
 };
 constexpr int kTcCtasPerSm = 3;  // persistent CTAs per SM (shared memory allows three at KB = 32)
 
-// Block fixed point: the exponent e with max |v| < 2^e (0 for an all-zero set).
+// Block fixed point: the exponent e with max |v| < 2^e, from the FP32 exponent field (max |v| in
+// [2^(E-127), 2^(E-126)) for a normal value with biased exponent E), clamped below at -100 so that
+// the scales 2^(24 - e) and 2^(e - 8) stay normal FP32 values; sets below 2^-100 (all-zero ones
+// included) get digits that are zero or carry their values at an absolute 2^-124.
 __device__ __forceinline__ int fixed_exponent(float amax) {
-  int e = 0;
-  if (amax > 0.f) frexpf(amax, &e);
-  return e;
+  const int E = (int)((__float_as_uint(amax) >> 23) & 0xFFu);
+  return max(E - 126, -100);
 }
 
-// The three digits of v in units of 2^(e - 24): v 2^(24 - e) rounded to nearest, then cut.
-__device__ __forceinline__ void digits3(float v, int e, float& d0, float& d1, float& d2) {
-  const int si = __float2int_rn(ldexpf(v, 24 - e));  // |si| <= 2^24
-  const int q0 = (si + (1 << 15)) >> 16;              // in [-256, 256]
-  const int r1 = si - (q0 << 16);                     // in [-2^15, 2^15)
-  const int q1 = (r1 + (1 << 7)) >> 8;                // in [-128, 128]
-  const int q2 = r1 - (q1 << 8);                      // in [-128, 128)
-  d0 = (float)q0;
-  d1 = (float)q1;
-  d2 = (float)q2;
+// 2^(24 - e) as an FP32 value (a power of two; e is at most 128 for finite inputs).
+__device__ __forceinline__ float fixed_scale(int e) { return __int_as_float((127 + 24 - e) << 23); }
+
+// Round to the nearest integer (ties to even) for |x| < 2^22: adding and removing 1.5 * 2^23 puts
+// the sum where the FP32 spacing is 1. Explicit round-to-nearest intrinsics keep the compiler from
+// folding the pair.
+__device__ __forceinline__ float round_int(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.f), 12582912.f);
+}
+
+// The three digits of v in units of 2^(e - 24), x = v 2^(24 - e) = sc * v (exact, |x| < 2^24):
+// q0 = round(x / 2^16), q1 = round((x - q0 2^16) / 2^8), q2 = round(x - q0 2^16 - q1 2^8), so that
+// q0 2^16 + q1 2^8 + q2 is x rounded to the nearest integer; every step is exact in FP32 except the
+// intended roundings, and each digit is a small integer (|q0| <= 256, |q1|, |q2| <= 128).
+__device__ __forceinline__ void digits3(float v, float sc, float& d0, float& d1, float& d2) {
+  const float x = v * sc;
+  d0 = round_int(x * (1.f / 65536.f));
+  const float r1 = fmaf(-d0, 65536.f, x);
+  d1 = round_int(r1 * (1.f / 256.f));
+  d2 = round_int(fmaf(-d1, 256.f, r1));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  // The digits are small integers: exactly representable in BF16, so truncating the FP32 bit
-  // pattern to its upper half is exact.
-  return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xFFFF0000u);
+  // The digits are small integers: exactly representable in BF16, so the upper halves of the FP32
+  // bit patterns are their BF16 encodings (one byte permute).
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// A CUtensorMap (128 bytes, 64-byte aligned) as the kernels see it: opaque.
+struct alignas(64) TcTensorMap {
+  unsigned char bytes[128];
+};
+
+// The 16-byte chunk where logical chunk q of tile row `row` lands under the tensor maps' swizzle
+// (128-byte swizzle for 128-byte rows, 64-byte swizzle for 64-byte rows).
+template <int KB>
+__device__ __forceinline__ int tc_swz(int row, int q) {
+  return KB == 32 ? (q ^ (row & 7)) : (q ^ ((row >> 1) & 3));
 }
 
 // Where rotation block b sits: its update, side, first row and row count.
@@ -116,6 +142,12 @@ struct TcBlock {
     const bool is_row = op.kind == kRow;
     return (pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V)) + base * KB;
   }
+  // The tensor map of the matrix the block rotates: maps[2 * stream + 0] covers U, [.. + 1] V.
+  __device__ __forceinline__ const void* tmap(const PoolOp* ops, const TcTensorMap* maps) const {
+    const PoolOp& op = ops[e];
+    const bool is_v = pside == (op.kind == kRow);
+    return &maps[2 * op.sid + (is_v ? 1 : 0)];
+  }
 };
 
 // First block at or after b (below b1) whose update has work (k_out >= 0), or b1.
@@ -128,11 +160,14 @@ __device__ __forceinline__ int tc_next_live(const RotScratch<KB>* scratch, const
 template <int KB>
 __global__ void __launch_bounds__(kTcRotThreads)
     k_pool_rotate_tc(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
-                     const int* __restrict__ chunk_start, const int* __restrict__ block_op, int nblocks) {
+                     const int* __restrict__ chunk_start, const int* __restrict__ block_op, int nblocks,
+                     const TcTensorMap* __restrict__ maps) {
   static_assert(KB == 16 || KB == 32, "tensor-core rotation buckets");
   using L = TcRotLayout<KB>;
   constexpr int C4 = KB / 4;  // float4 chunks per row
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // The swizzled TMA boxes need a 1 KiB aligned destination.
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   auto stage_buf = [&](int st_) { return reinterpret_cast<float*>(smem + (uint32_t)st_ * L::kTile); };
   unsigned char* Ad = smem + L::kOffA;
   unsigned char* Bd = smem + L::kOffB;
@@ -169,8 +204,10 @@ __global__ void __launch_bounds__(kTcRotThreads)
   uint32_t mma_uses = 0;
   bool mma_inflight = false;
   if (tid == 0) {
-    tc::mbar_arrive_expect_tx(&full[0], (uint32_t)blk.rows * KB * 4);
-    tc::bulk_g2s(stage_buf(0), blk.tile(ops), (uint32_t)blk.rows * KB * 4, &full[0]);
+    const void* tm = blk.tmap(ops, maps);
+    tc::fence_tensormap_acquire(tm);
+    tc::mbar_arrive_expect_tx(&full[0], L::kTile);
+    tc::tma_load_2d(stage_buf(0), tm, 0, (int)blk.base, &full[0]);
   }
   inflight0 = true;
   int stage = 0, prev_e = -1;
@@ -181,9 +218,12 @@ __global__ void __launch_bounds__(kTcRotThreads)
     if (nxt < b1) {
       nb.locate(ops, scratch, chunk_start, block_op, nxt);
       if (tid == 0) {
-        tc::bulk_wait_read_all();  // the other stage's last store has been read out of shared memory
-        tc::mbar_arrive_expect_tx(&full[stage ^ 1], (uint32_t)nb.rows * KB * 4);
-        tc::bulk_g2s(stage_buf(stage ^ 1), nb.tile(ops), (uint32_t)nb.rows * KB * 4, &full[stage ^ 1]);
+        // The other stage was last read by the previous block's row loads, before barriers since.
+        tc::fence_proxy_async_smem();
+        const void* tm = nb.tmap(ops, maps);
+        tc::fence_tensormap_acquire(tm);
+        tc::mbar_arrive_expect_tx(&full[stage ^ 1], L::kTile);
+        tc::tma_load_2d(stage_buf(stage ^ 1), tm, 0, (int)nb.base, &full[stage ^ 1]);
       }
       if (stage) inflight0 = true;
       else inflight1 = true;
@@ -210,11 +250,12 @@ __global__ void __launch_bounds__(kTcRotThreads)
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 2));
         const int eb = fixed_exponent(amax);
-        if (sub == 0) bscale[jj] = ldexpf(1.f, eb - 8);
+        if (sub == 0) bscale[jj] = __int_as_float((127 + eb - 8) << 23);
+        const float scb = fixed_scale(eb);
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
           float d0, d1, d2;
-          digits3(v[q], eb, d0, d1, d2);
+          digits3(v[q], scb, d0, d1, d2);
           const uint32_t o = tc::kmajor_offset16(jj, sub * RPT + q, KB);
           *reinterpret_cast<uint16_t*>(Bd + o) = (uint16_t)(__float_as_uint(d0) >> 16);
           *reinterpret_cast<uint16_t*>(Bd + L::kBplane + o) = (uint16_t)(__float_as_uint(d1) >> 16);
@@ -250,27 +291,12 @@ __global__ void __launch_bounds__(kTcRotThreads)
     float xv[KB];
 #pragma unroll
     for (int q = 0; q < C4; ++q) {
-      // chunk (q + row) mod C4 first: conflict-free across the warp; the chunk order is undone by a
-      // barrel shift so that register indices stay static
-      const int qq = (q + row) % C4;
-      const float4 a = live ? T4[row * C4 + qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // the swizzle spreads a warp's reads of chunk q over all banks
+      const float4 a = live ? T4[row * C4 + tc_swz<KB>(row, q)] : make_float4(0.f, 0.f, 0.f, 0.f);
       xv[4 * q] = a.x;
       xv[4 * q + 1] = a.y;
       xv[4 * q + 2] = a.z;
       xv[4 * q + 3] = a.w;
-    }
-    {
-      const int sh = row % C4;
-#pragma unroll
-      for (int b = 1; b < C4; b <<= 1) {
-        if (sh & b) {
-          float tmp[KB];
-#pragma unroll
-          for (int i = 0; i < KB; ++i) tmp[i] = xv[(i - 4 * b + KB) % KB];
-#pragma unroll
-          for (int i = 0; i < KB; ++i) xv[i] = tmp[i];
-        }
-      }
     }
     float amax = 0.f;
 #pragma unroll
@@ -292,15 +318,16 @@ __global__ void __launch_bounds__(kTcRotThreads)
       zh = (sacc.hi + sacc.lo) * sc.inv_rho;
     }
     const int ea = fixed_exponent(amax);
-    const float ascale = ldexpf(1.f, ea - 8);
+    const float ascale = __int_as_float((127 + ea - 8) << 23);
+    const float sca = fixed_scale(ea);
 #pragma unroll
     for (int g = 0; g < KB / 8; ++g) {  // one 16-byte core-matrix row per digit plane
       uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         float a0, a1, a2, c0, c1, c2;
-        digits3(xv[8 * g + 2 * h], ea, a0, a1, a2);
-        digits3(xv[8 * g + 2 * h + 1], ea, c0, c1, c2);
+        digits3(xv[8 * g + 2 * h], sca, a0, a1, a2);
+        digits3(xv[8 * g + 2 * h + 1], sca, c0, c1, c2);
         w0[h] = pack_bf16x2(a0, c0);
         w1[h] = pack_bf16x2(a1, c1);
         w2[h] = pack_bf16x2(a2, c2);
@@ -370,30 +397,14 @@ __global__ void __launch_bounds__(kTcRotThreads)
         acc[j] = y;
       }
       if (live) {
-        const int sh = row % C4;
+        // straight to global memory: a warp's stores cover its 32 rows' 128-byte lines in C4 steps
+        float4* W4 = reinterpret_cast<float4*>(blk.tile(ops) + (int64_t)row * KB);
 #pragma unroll
-        for (int b = 1; b < C4; b <<= 1) {
-          if (sh & b) {
-            float tmp[KB];
-#pragma unroll
-            for (int i = 0; i < KB; ++i) tmp[i] = acc[(i + 4 * b) % KB];
-#pragma unroll
-            for (int i = 0; i < KB; ++i) acc[i] = tmp[i];
-          }
-        }
-        float4* W4 = reinterpret_cast<float4*>(T);
-#pragma unroll
-        for (int q = 0; q < C4; ++q)
-          W4[row * C4 + (q + sh) % C4] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        for (int q = 0; q < C4; ++q) W4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
       }
     }
-    tc::fence_proxy_async_smem();
     tc::tc_fence_before_sync();
-    __syncthreads();  // the tile is complete, and every warp is done with the accumulators
-    if (tid == 0) {
-      tc::bulk_s2g(blk.tile(ops), T, (uint32_t)blk.rows * KB * 4);
-      tc::bulk_commit();
-    }
+    __syncthreads();  // every warp is done with the accumulators
     stage ^= 1;
     cur = nxt;
     if (cur < b1) blk = nb;
@@ -405,7 +416,6 @@ __global__ void __launch_bounds__(kTcRotThreads)
     if (inflight1) tc::mbar_wait_bounded(&full[1], use1 & 1u, kTcWaitNs);
     if (mma_inflight) tc::mbar_wait_bounded(mmab, mma_uses & 1u, kTcWaitNs);
   }
-  if (tid == 0) tc::bulk_wait_all();
   tc::tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) {

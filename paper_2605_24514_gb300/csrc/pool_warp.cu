@@ -34,12 +34,13 @@ int device_sms() {
 }
 template <int KB>
 void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
-                      const int* block_op) {
+                      const int* block_op, const void* tmaps) {
   // Persistent CTAs: a few per SM, each over a contiguous range of the rotation blocks.
   const int grid = std::min(nblocks, kTcCtasPerSm * device_sms());
   if (grid <= 0) return;
   k_pool_rotate_tc<KB><<<grid, kTcRotThreads, TcRotLayout<KB>::kBytes, s>>>(
-      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks);
+      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks,
+      reinterpret_cast<const TcTensorMap*>(tmaps));
 }
 }  // namespace
 
@@ -56,15 +57,15 @@ cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* op
 int pool_rot_rows(int kb, bool use_tc) { return use_tc && (kb == 16 || kb == 32) ? kTcRotRows : kPoolRotRows; }
 
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
-                               const int* chunks, const int* block_op, bool use_tc) {
+                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps) {
   switch (kb) {
     case 8: rotate_launch<8>(nblocks, s, ops, scratch, chunks, block_op); break;
     case 16:
-      if (use_tc) rotate_tc_launch<16>(nblocks, s, ops, scratch, chunks, block_op);
+      if (use_tc) rotate_tc_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
       else rotate_launch<16>(nblocks, s, ops, scratch, chunks, block_op);
       break;
     default:
-      if (use_tc) rotate_tc_launch<32>(nblocks, s, ops, scratch, chunks, block_op);
+      if (use_tc) rotate_tc_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
       else rotate_launch<32>(nblocks, s, ops, scratch, chunks, block_op);
       break;
   }
@@ -153,3 +154,17 @@ cudaError_t pool_warp_set_attrs() {
 }
 
 }  // namespace isvd
+
+#ifdef ISVD_CORE_TIMING
+// Phase timing of this translation unit's kernels (its own copies of the stamp counters).
+extern "C" int isvd_debug_warp_clock_sums(unsigned long long* out, int reset) {
+  int e = (int)cudaMemcpyFromSymbol(out, isvd::isvd_core_clock_sum, sizeof(unsigned long long) * 32);
+  if (!e) e = (int)cudaMemcpyFromSymbol(out + 32, isvd::isvd_core_clock_cnt, sizeof(unsigned long long) * 32);
+  if (!e && reset) {
+    unsigned long long z[32] = {};
+    e = (int)cudaMemcpyToSymbol(isvd::isvd_core_clock_sum, z, sizeof(z));
+    if (!e) e = (int)cudaMemcpyToSymbol(isvd::isvd_core_clock_cnt, z, sizeof(z));
+  }
+  return e;
+}
+#endif
