@@ -57,7 +57,7 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) of one launch from the ncu --set full capture summarised under
 # profiles/ (tick 1 of the default workload; later ticks differ by < 1%). Set to None whenever
 # the kernel changes until it is captured again.
-DRAM_TRAFFIC = {"k_pool_rotate<32>": 243461376, "k_pool_rotate_tc<32>": None}
+DRAM_TRAFFIC = {"k_pool_rotate<32>": None, "k_pool_rotate_tc<32>": None}
 
 
 def measured_peaks():
@@ -325,7 +325,8 @@ def run_batched(args):
     ks = rng.choice(np.asarray(W["ks"]), size=S)
     st = torch.cuda.Stream()
     pool = pkg.Pool(k_max=int(max(W["ks"])), stream=st.cuda_stream,
-                    flags=pkg.POOL_COMPLETIONS | (pkg.POOL_SIMT_ROTATIONS if args.simt_rotations else 0))
+                    flags=pkg.POOL_COMPLETIONS | pkg.POOL_DEVICE_CHECKS |
+                    (pkg.POOL_TC_ROTATIONS if args.tc_rotations else 0))
     t0 = time.perf_counter()
     ids, rows, payload_parts, offs = [], [], [], []
     for sidx in range(S):
@@ -507,7 +508,7 @@ def run_batched(args):
     dom = max((c for c in class_bytes if prof.get(c, (0.0, 0))[1] > 0), key=lambda c: class_bytes[c])
     dom_ms, dom_n = prof[dom]
     ach = class_bytes.get(dom, 0.0) / (dom_ms / dom_n * 1e6) if dom in class_bytes else 0.0
-    tc = "" if args.simt_rotations else "_tc"
+    tc = "_tc" if args.tc_rotations else ""
     kernel_names = {"warp8": "k_pool_warp<8>", "warp16": "k_pool_warp<16>", "warp32": "k_pool_warp<32>",
                     "rot8": "k_pool_rotate<8>", "rot16": f"k_pool_rotate{tc}<16>", "rot32": f"k_pool_rotate{tc}<32>",
                     "retry": "k_pool_retry<32>", "cta": "k_pool_tick"}
@@ -889,8 +890,8 @@ def main():
     ap.add_argument("--acc-streams", type=int, default=8)
     ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests per second")
-    ap.add_argument("--simt-rotations", action="store_true",
-                    help="batched workload: rotate on the FP32 pipes in every rank bucket")
+    ap.add_argument("--tc-rotations", action="store_true",
+                    help="batched workload: rotate rank buckets 16 and 32 on the tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -263,11 +263,16 @@ typedef struct {
 } isvd_pool_config;
 
 /* isvd_pool_config.flags */
-#define ISVD_POOL_SIMT_ROTATIONS 1  /* rotate on the FP32 pipes in every rank bucket (default: the
-                                       tensor-core rotation with exact BF16 digit products for
-                                       buckets 16 and 32) */
+#define ISVD_POOL_TC_ROTATIONS 1    /* rotate rank buckets 16 and 32 on the tensor cores (exact
+                                       BF16 digit products; same accuracy class, measured slower at
+                                       these ranks). Default: FP32 pipes in every bucket */
 #define ISVD_POOL_COMPLETIONS 2     /* every op of a submit leaves a completion record for
                                        isvd_pool_poll */
+#define ISVD_POOL_DEVICE_CHECKS 4   /* a host payload is not scanned on the host: non-finite values
+                                       are caught by the kernels, as for a device payload (a sticky
+                                       ISVD_ENONFINITE of that stream at the next isvd_pool_sync,
+                                       and status ISVD_ENONFINITE in the op's completion record);
+                                       submit then costs no pass over the payload on the host */
 
 /* Completion record of one pool op (ISVD_POOL_COMPLETIONS). */
 typedef struct {
@@ -310,9 +315,13 @@ isvd_status isvd_pool_release(isvd_pool_t p, int32_t stream_id);
 /* Queues ops (see above). All ops are validated (stream, kind, shape, bounds, finite deltas)
  * before any work is queued; on error nothing is queued. payload is FP32, host or device memory
  * (payload_on_device). A host payload is also scanned for NaN/Inf first (ISVD_ENONFINITE, nothing
- * queued; the scan reads the whole payload once). A device payload is not read by the host: a
- * non-finite value there is seen by the kernels and reported as a sticky ISVD_ENONFINITE of that
- * stream by the next isvd_pool_sync, as for device inputs of a single stream. */
+ * queued; the scan reads the whole payload once), unless the pool has ISVD_POOL_DEVICE_CHECKS.
+ * A host payload is copied on the pool's CUDA stream: from pageable memory before the call
+ * returns, from page-locked memory when the stream reaches the copy (keep such a buffer unchanged
+ * until then, e.g. until isvd_pool_sync or the ops' completion records). A device payload is not
+ * read by the host: a non-finite value there is seen by the kernels and reported as a sticky
+ * ISVD_ENONFINITE of that stream by the next isvd_pool_sync, as for device inputs of a single
+ * stream. */
 isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, const void* payload,
                              int64_t payload_len, int payload_on_device);
 

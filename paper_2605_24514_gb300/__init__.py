@@ -67,8 +67,9 @@ class PoolConfig(C.Structure):
                 ("tau_evr", C.c_double)]
 
 
-POOL_SIMT_ROTATIONS = 1
+POOL_TC_ROTATIONS = 1
 POOL_COMPLETIONS = 2
+POOL_DEVICE_CHECKS = 4
 COMPLETION_DTYPE = np.dtype([("seq", np.int64), ("stream", np.int32), ("kind", np.int32), ("status", np.int32),
                              ("r", np.int32), ("rho", np.float64), ("sigma_max", np.float64), ("done_ns", np.uint64)])
 

@@ -543,6 +543,7 @@ isvd_status read_state(isvd_ctx* h, DevState* out) {
   if (out->status & kStNonFinite) return fail(h, ISVD_ENONFINITE, "non-finite value in a device input");
   if (out->status & kStNotConv) return fail(h, ISVD_ENOTCONV, "core Jacobi SVD did not converge");
   if (out->status & kStTimeout) return fail(h, ISVD_ETIMEOUT, "device wait timed out");
+  if (out->status & kStLayout) return fail(h, ISVD_ECUDA, "kernel shared-memory layout did not fit its launch");
   return ISVD_OK;
 }
 
@@ -1473,6 +1474,9 @@ struct isvd_pool_ctx {
   DevState* zero_st = nullptr;
   double* gather_dev = nullptr;
   int64_t gather_cap = 0;
+  int* status_dev = nullptr;   // every slot's status word (isvd_pool_sync), device and pinned host
+  int* status_host = nullptr;
+  int64_t status_cap = 0;
   // Tensor maps (CUtensorMap, 128 bytes) of every slot's U and V for the tensor-core rotations
   // (TMA loads of 128-row boxes, swizzled), rebuilt when a stream's U or V is reallocated.
   CUtensorMap* tmaps_dev = nullptr;
@@ -1603,7 +1607,7 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
   void* scr = static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
   cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op,
-                                   pool_rot_rows(KB, !(p->flags & ISVD_POOL_SIMT_ROTATIONS)));
+                                   pool_rot_rows(KB, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0));
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1616,7 +1620,7 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
                                const int* block_op, int nblocks) {
   const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
-  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, !(p->flags & ISVD_POOL_SIMT_ROTATIONS),
+  cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0,
                                      p->tmaps_dev);
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
@@ -1679,26 +1683,29 @@ EncodeTiledFn encode_tiled() {
     tried = true;
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeTiledFn>(f);
   }
   return fn;
 }
 
-// A map over a rows x ld FP32 matrix (row-major) with 128-row boxes of the full row width: 128-byte
-// swizzle for 128-byte rows, 64-byte swizzle for 64-byte rows (the widths the tensor-core rotation
-// serves); zeroed for other widths (never used). Rows beyond `rows` read as zeros.
+// A map over a rows x ld FP32 matrix (row-major) with boxes of kRowBoxRows rows of the full row
+// width, swizzled by the row width (32-, 64- or 128-byte rows: the rank buckets 8, 16, 32 the
+// rotation kernels serve) so that a thread reading its own staged row meets no bank conflicts;
+// zeroed for other widths (never used).
 bool encode_rows_map(CUtensorMap* m, const void* base, int64_t rows, int ld) {
   memset(m, 0, sizeof(*m));
-  if (ld != 16 && ld != 32) return true;
+  if (ld != 8 && ld != 16 && ld != 32) return true;
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)ld, 128u};
+  const cuuint32_t box[2] = {(cuuint32_t)ld, (cuuint32_t)kRowBoxRows};
   const cuuint32_t estr[2] = {1u, 1u};
-  const CUtensorMapSwizzle sw = ld == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUtensorMapSwizzle sw = ld == 32   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : ld == 16 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                           : CU_TENSOR_MAP_SWIZZLE_32B;
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1748,6 +1755,7 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (!cfg || !out) return ISVD_EINVAL;
   *out = nullptr;
   if (cfg->k_max < 1 || cfg->k_max > kKmaxLimit) return ISVD_EINVAL;
+  if (cfg->flags & ~(ISVD_POOL_TC_ROTATIONS | ISVD_POOL_COMPLETIONS | ISVD_POOL_DEVICE_CHECKS)) return ISVD_EINVAL;
   isvd_pool_ctx* p = new isvd_pool_ctx();
   p->kmax = cfg->k_max;
   p->kb = kb_bucket(cfg->k_max);
@@ -1830,6 +1838,8 @@ void isvd_pool_destroy(isvd_pool_t p) {
   if (p->zero_sig) cudaFree(p->zero_sig);
   if (p->zero_st) cudaFree(p->zero_st);
   if (p->gather_dev) cudaFree(p->gather_dev);
+  if (p->status_dev) cudaFree(p->status_dev);
+  if (p->status_host) cudaFreeHost(p->status_host);
   if (p->tmaps_dev) cudaFree(p->tmaps_dev);
   for (auto& sg : p->stage) {
     if (sg.ops) cudaFreeHost(sg.ops);
@@ -2013,7 +2023,7 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     tick_of[e] = seen[sid]++;
     nticks = std::max(nticks, tick_of[e] + 1);
   }
-  if (!payload_on_device && payload_len > 0 &&
+  if (!payload_on_device && payload_len > 0 && !(p->flags & ISVD_POOL_DEVICE_CHECKS) &&
       !host_finite((const float*)payload, payload_len))
     return pool_fail(p, ISVD_ENONFINITE, "pool payload has non-finite values");
   const float* pay = (const float*)payload;
@@ -2273,7 +2283,7 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       while (b1 < tick_start[t + 1] && fused[b1] == 2 && bucket_at(b1) == bucket_at(q)) {
         const PoolOp& d = sg.ops[b1];
         const int64_t nP = d.kind == kRow ? d.n : d.m, nQ = d.kind == kRow ? d.m : d.n;
-        const int rr = pool_rot_rows(bucket_at(q), !(p->flags & ISVD_POOL_SIMT_ROTATIONS));
+        const int rr = pool_rot_rows(bucket_at(q), (p->flags & ISVD_POOL_TC_ROTATIONS) != 0);
         sg.chunks[b1] = tot;
         tot += (int)((nP + rr - 1) / rr + (nQ + rr - 1) / rr);
         ++b1;
@@ -2470,9 +2480,34 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
 
 isvd_status isvd_pool_sync(isvd_pool_t p) {
   if (!p) return ISVD_EINVAL;
+  // Every slot's status word in one gather and one copy; only a stream whose word is set is read
+  // in full (its sticky error).
+  const int64_t n = std::min<int64_t>((int64_t)p->streams.size(), p->tab_cap);
+  if (n > p->status_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->status_dev) cudaFree(p->status_dev);
+    if (p->status_host) cudaFreeHost(p->status_host);
+    p->status_dev = nullptr;
+    p->status_host = nullptr;
+    p->status_cap = std::max<int64_t>(n, 2 * p->status_cap);
+    if (cudaMalloc((void**)&p->status_dev, sizeof(int) * (size_t)p->status_cap) != cudaSuccess ||
+        cudaMallocHost((void**)&p->status_host, sizeof(int) * (size_t)p->status_cap) != cudaSuccess) {
+      p->status_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool status words");
+    }
+  }
+  if (n > 0) {
+    const cudaError_t e = pool_gather_status_launch(n, p->stream, p->tab_st, p->status_dev);
+    if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool status gather: ") + cudaGetErrorString(e));
+    p->launches++;
+    if (cudaMemcpyAsync(p->status_host, p->status_dev, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, p->stream) !=
+        cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool status copy");
+  }
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool sync");
-  for (isvd_ctx* h : p->streams) {
-    if (!h) continue;
+  for (int64_t i = 0; i < (int64_t)p->streams.size(); ++i) {
+    isvd_ctx* h = p->streams[i];
+    if (!h || (i < n && p->status_host[i] == 0)) continue;
     DevState ds;
     isvd_status s = read_state(h, &ds);
     if (s) return s;

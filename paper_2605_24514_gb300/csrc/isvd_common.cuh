@@ -15,6 +15,7 @@ constexpr int kMaxProjBlocks = 256;
 constexpr int kStNotConv = 1;
 constexpr int kStNonFinite = 2;
 constexpr int kStTimeout = 4;
+constexpr int kStLayout = 8;  // a kernel's shared-memory layout did not fit its launch (nothing done)
 
 // Update kinds (Section 2.1).
 constexpr int kRow = 0;

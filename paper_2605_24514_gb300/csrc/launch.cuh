@@ -56,6 +56,8 @@ struct PoolRankOp;
 // k <- min(k + 1, kcap) for every listed stream whose EVR = sum sigma^2 / N_t is below tau.
 cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau);
 cudaError_t pool_complete_launch(int count, cudaStream_t s, const PoolOp* ops, PoolCompletion* out);
+// out[s] = the status word of slot s's device state, s < n.
+cudaError_t pool_gather_status_launch(int64_t n, cudaStream_t s, const DevState* const* st, int* out);
 cudaError_t pool_gather_sigma_launch(int64_t n, cudaStream_t s, const double* const* sig, const DevState* const* st,
                                      int ld, double* out);
 

@@ -10,6 +10,9 @@
 
 namespace isvd {
 
+// Rows per TMA box of the pools' row tensor maps over U and V (row width = the rank bucket).
+constexpr int kRowBoxRows = 32;
+
 // One update of one stream, as the fused kernel reads it.
 struct PoolOp {
   float* U;            // m x r (row stride ld)

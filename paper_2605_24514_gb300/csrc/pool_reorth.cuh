@@ -53,12 +53,8 @@ __device__ inline void reorth_gram(const float* Q, int64_t rows, int ld, int r, 
     }
   }
   double acc[kReorthPairs];
-  float part[kReorthPairs];
 #pragma unroll
-  for (int q = 0; q < kReorthPairs; ++q) {
-    acc[q] = 0.0;
-    part[q] = 0.f;
-  }
+  for (int q = 0; q < kReorthPairs; ++q) acc[q] = 0.0;
   const int c4 = ld / 4;
   for (int64_t r0 = 0; r0 < rows; r0 += kReorthChunk) {
     const int nr = (int)(rows - r0 < kReorthChunk ? rows - r0 : kReorthChunk);

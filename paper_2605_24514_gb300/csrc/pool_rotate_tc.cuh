@@ -24,10 +24,10 @@
 // update tables, 128 rows per block for these buckets). Persistent CTAs of 128 threads (a few per
 // SM) each take a contiguous range of blocks, so consecutive blocks mostly share their update and
 // side and the core factor's digit planes are cut once per run of blocks. Per block:
-//   1. the block's row tile (a 128-row box of the stream's U or V, through the pool's tensor map
-//      of that matrix: a TMA load, swizzled so that a thread reading its row meets no bank
-//      conflicts, rows past the matrix read as zeros) was brought into one of two shared-memory
-//      stages one block ahead; the next block's load is issued now;
+//   1. the block's rows (the 32-row boxes of the stream's U or V that hold them, through the
+//      pool's tensor map of that matrix: TMA loads, swizzled so that a thread reading its row
+//      meets no bank conflicts) were brought into one of two shared-memory stages one block
+//      ahead; the next block's loads are issued now;
 //   2. if the update or side changed: the core factor (V_K or U_K; rows >= r and columns >= k_out
 //      zeroed) is cut into digit planes (B operands, K-major) with per-column scales, four threads
 //      per column;
@@ -43,14 +43,12 @@
 // the CTA stops, waits (bounded) for its copies, frees its TMEM and returns.
 #pragma once
 
-#include "pool_warp.cuh"
-#include "tc_ptx.cuh"
+#include "pool_rotate_tma.cuh"
 
 namespace isvd {
 
 constexpr int kTcRotRows = 128;                        // rows per CTA (one per thread)
 constexpr int kTcRotThreads = kTcRotRows;
-constexpr uint64_t kTcWaitNs = 2000ull * 1000 * 1000;  // 2 s
 
 template <int KB>
 struct TcRotLayout {
@@ -105,63 +103,24 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// A CUtensorMap (128 bytes, 64-byte aligned) as the kernels see it: opaque.
-struct alignas(64) TcTensorMap {
-  unsigned char bytes[128];
-};
-
-// The 16-byte chunk where logical chunk q of tile row `row` lands under the tensor maps' swizzle
-// (128-byte swizzle for 128-byte rows, 64-byte swizzle for 64-byte rows).
+// Thread 0: the TMA loads of block bk's rows (32-row boxes, only those holding live rows) into
+// stage buffer dst, completing on bar.
 template <int KB>
-__device__ __forceinline__ int tc_swz(int row, int q) {
-  return KB == 32 ? (q ^ (row & 7)) : (q ^ ((row >> 1) & 3));
-}
-
-// Where rotation block b sits: its update, side, first row and row count.
-template <int KB>
-struct TcBlock {
-  int e, rows;
-  bool pside, withz;
-  int64_t base;
-  __device__ __forceinline__ void locate(const PoolOp* ops, const RotScratch<KB>* scratch, const int* chunk_start,
-                                         const int* block_op, int b) {
-    e = block_op[b];
-    const PoolOp& op = ops[e];
-    const bool is_row = op.kind == kRow;
-    const int64_t nP = is_row ? op.n : op.m, nQ = is_row ? op.m : op.n;
-    const int cP = (int)((nP + kTcRotRows - 1) / kTcRotRows);
-    const int ci = b - chunk_start[e];
-    pside = ci < cP;
-    withz = pside && scratch[e].grew;
-    const int64_t nrows = pside ? nP : nQ;
-    base = (int64_t)(pside ? ci : ci - cP) * kTcRotRows;
-    rows = (int)(nrows - base < kTcRotRows ? nrows - base : kTcRotRows);
-  }
-  __device__ __forceinline__ float* tile(const PoolOp* ops) const {
-    const PoolOp& op = ops[e];
-    const bool is_row = op.kind == kRow;
-    return (pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V)) + base * KB;
-  }
-  // The tensor map of the matrix the block rotates: maps[2 * stream + 0] covers U, [.. + 1] V.
-  __device__ __forceinline__ const void* tmap(const PoolOp* ops, const TcTensorMap* maps) const {
-    const PoolOp& op = ops[e];
-    const bool is_v = pside == (op.kind == kRow);
-    return &maps[2 * op.sid + (is_v ? 1 : 0)];
-  }
-};
-
-// First block at or after b (below b1) whose update has work (k_out >= 0), or b1.
-template <int KB>
-__device__ __forceinline__ int tc_next_live(const RotScratch<KB>* scratch, const int* block_op, int b, int b1) {
-  while (b < b1 && scratch[block_op[b]].k_out < 0) ++b;
-  return b;
+__device__ __forceinline__ void tc_issue_rows(const RotBlock<KB, kTcRotRows>& bk, const PoolOp* ops,
+                                              const RowTensorMap* maps, float* dst, uint64_t* bar) {
+  const int nbox = (bk.rows + kRowBoxRows - 1) / kRowBoxRows;
+  tc::mbar_arrive_expect_tx(bar, (uint32_t)nbox * (kRowBoxRows * KB * 4));
+  const void* tm = bk.tmap(ops, maps);
+  tc::fence_tensormap_acquire(tm);
+  for (int b = 0; b < nbox; ++b)
+    tc::tma_load_2d(dst + b * kRowBoxRows * KB, tm, 0, (int)bk.base + b * kRowBoxRows, bar);
 }
 
 template <int KB>
 __global__ void __launch_bounds__(kTcRotThreads)
     k_pool_rotate_tc(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
                      const int* __restrict__ chunk_start, const int* __restrict__ block_op, int nblocks,
-                     const TcTensorMap* __restrict__ maps) {
+                     const RowTensorMap* __restrict__ maps) {
   static_assert(KB == 16 || KB == 32, "tensor-core rotation buckets");
   using L = TcRotLayout<KB>;
   constexpr int C4 = KB / 4;  // float4 chunks per row
@@ -182,7 +141,7 @@ __global__ void __launch_bounds__(kTcRotThreads)
 
   const int per = (nblocks + (int)gridDim.x - 1) / (int)gridDim.x;
   const int b1 = min(nblocks, ((int)blockIdx.x + 1) * per);
-  int cur = tc_next_live<KB>(scratch, block_op, (int)blockIdx.x * per, b1);
+  int cur = rot_next_live<KB>(scratch, block_op, (int)blockIdx.x * per, b1);
   if (cur >= b1) return;  // uniform: nothing to rotate in this range
 
   if (tid == 0) {
@@ -197,33 +156,25 @@ __global__ void __launch_bounds__(kTcRotThreads)
   tc::tc_fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  TcBlock<KB> blk;
+  RotBlock<KB, kTcRotRows> blk;
   blk.locate(ops, scratch, chunk_start, block_op, cur);
   uint32_t use0 = 0u, use1 = 0u;              // completed loads per stage (mbarrier parity)
   bool inflight0 = false, inflight1 = false;  // a load issued into the stage and not yet waited for
   uint32_t mma_uses = 0;
   bool mma_inflight = false;
-  if (tid == 0) {
-    const void* tm = blk.tmap(ops, maps);
-    tc::fence_tensormap_acquire(tm);
-    tc::mbar_arrive_expect_tx(&full[0], L::kTile);
-    tc::tma_load_2d(stage_buf(0), tm, 0, (int)blk.base, &full[0]);
-  }
+  if (tid == 0) tc_issue_rows<KB>(blk, ops, maps, stage_buf(0), &full[0]);
   inflight0 = true;
   int stage = 0, prev_e = -1;
   bool prev_side = false, failed = false;
   while (cur < b1) {
-    const int nxt = tc_next_live<KB>(scratch, block_op, cur + 1, b1);
-    TcBlock<KB> nb;
+    const int nxt = rot_next_live<KB>(scratch, block_op, cur + 1, b1);
+    RotBlock<KB, kTcRotRows> nb;
     if (nxt < b1) {
       nb.locate(ops, scratch, chunk_start, block_op, nxt);
       if (tid == 0) {
         // The other stage was last read by the previous block's row loads, before barriers since.
         tc::fence_proxy_async_smem();
-        const void* tm = nb.tmap(ops, maps);
-        tc::fence_tensormap_acquire(tm);
-        tc::mbar_arrive_expect_tx(&full[stage ^ 1], L::kTile);
-        tc::tma_load_2d(stage_buf(stage ^ 1), tm, 0, (int)nb.base, &full[stage ^ 1]);
+        tc_issue_rows<KB>(nb, ops, maps, stage_buf(stage ^ 1), &full[stage ^ 1]);
       }
       if (stage) inflight0 = true;
       else inflight1 = true;
@@ -270,7 +221,7 @@ __global__ void __launch_bounds__(kTcRotThreads)
       prev_e = blk.e;
       prev_side = blk.pside;
     }
-    const bool got = tc::mbar_wait_bounded(&full[stage], (stage ? use1 : use0) & 1u, kTcWaitNs);
+    const bool got = tc::mbar_wait_bounded(&full[stage], (stage ? use1 : use0) & 1u, kRotWaitNs);
     if (__syncthreads_or(!got)) {  // also: the B planes, scales, z row and p are complete
       failed = true;
       break;
@@ -292,7 +243,7 @@ __global__ void __launch_bounds__(kTcRotThreads)
 #pragma unroll
     for (int q = 0; q < C4; ++q) {
       // the swizzle spreads a warp's reads of chunk q over all banks
-      const float4 a = live ? T4[row * C4 + tc_swz<KB>(row, q)] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 a = live ? T4[row * C4 + rows_swz<KB>(row, q)] : make_float4(0.f, 0.f, 0.f, 0.f);
       xv[4 * q] = a.x;
       xv[4 * q + 1] = a.y;
       xv[4 * q + 2] = a.z;
@@ -365,7 +316,7 @@ __global__ void __launch_bounds__(kTcRotThreads)
       tc::mma_commit(mmab);
     }
     mma_inflight = true;
-    const bool done = tc::mbar_wait_bounded(mmab, mma_uses & 1u, kTcWaitNs);
+    const bool done = tc::mbar_wait_bounded(mmab, mma_uses & 1u, kRotWaitNs);
     if (__syncthreads_or(!done)) {
       failed = true;
       break;
@@ -412,9 +363,9 @@ __global__ void __launch_bounds__(kTcRotThreads)
   if (failed && tid == 0) {
     atomicOr(&ops[blk.e].st->status, kStTimeout);
     // let the copies and MMAs in flight finish (bounded) before the CTA's memory goes away
-    if (inflight0) tc::mbar_wait_bounded(&full[0], use0 & 1u, kTcWaitNs);
-    if (inflight1) tc::mbar_wait_bounded(&full[1], use1 & 1u, kTcWaitNs);
-    if (mma_inflight) tc::mbar_wait_bounded(mmab, mma_uses & 1u, kTcWaitNs);
+    if (inflight0) tc::mbar_wait_bounded(&full[0], use0 & 1u, kRotWaitNs);
+    if (inflight1) tc::mbar_wait_bounded(&full[1], use1 & 1u, kRotWaitNs);
+    if (mma_inflight) tc::mbar_wait_bounded(mmab, mma_uses & 1u, kRotWaitNs);
   }
   tc::tc_fence_before_sync();
   __syncthreads();

@@ -17,12 +17,6 @@ void warp_launch(int count, cudaStream_t s, const PoolOp* ops, int base, int* re
   k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), s>>>(
       ops, count, base, retry, retry_n, reinterpret_cast<RotScratch<KB>*>(scratch), chunks, block_op, rot_rows);
 }
-template <int KB>
-void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
-                   const int* block_op) {
-  k_pool_rotate<KB><<<nblocks, kPoolRotThreads, rot_smem_bytes<KB>(), s>>>(
-      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op);
-}
 int device_sms() {
   static int sms = 0;
   if (sms == 0) {
@@ -32,6 +26,23 @@ int device_sms() {
   }
   return sms;
 }
+// Persistent CTAs over contiguous ranges of the rotation blocks: as many as fit on the SMs.
+template <int KB>
+void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
+                   const int* block_op, const void* tmaps) {
+  static int per_sm = 0;
+  if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pool_rotate<KB>, kRotThreadsAll,
+                                                                    RotTmaLayout<KB>::kBytes) != cudaSuccess ||
+                      per_sm < 1)) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int grid = std::min(nblocks, per_sm * device_sms());
+  if (grid <= 0) return;
+  k_pool_rotate<KB><<<grid, kRotThreadsAll, RotTmaLayout<KB>::kBytes, s>>>(
+      ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks,
+      reinterpret_cast<const RowTensorMap*>(tmaps));
+}
 template <int KB>
 void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
                       const int* block_op, const void* tmaps) {
@@ -40,7 +51,7 @@ void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void
   if (grid <= 0) return;
   k_pool_rotate_tc<KB><<<grid, kTcRotThreads, TcRotLayout<KB>::kBytes, s>>>(
       ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks,
-      reinterpret_cast<const TcTensorMap*>(tmaps));
+      reinterpret_cast<const RowTensorMap*>(tmaps));
 }
 }  // namespace
 
@@ -59,14 +70,14 @@ int pool_rot_rows(int kb, bool use_tc) { return use_tc && (kb == 16 || kb == 32)
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
                                const int* chunks, const int* block_op, bool use_tc, const void* tmaps) {
   switch (kb) {
-    case 8: rotate_launch<8>(nblocks, s, ops, scratch, chunks, block_op); break;
+    case 8: rotate_launch<8>(nblocks, s, ops, scratch, chunks, block_op, tmaps); break;
     case 16:
       if (use_tc) rotate_tc_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
-      else rotate_launch<16>(nblocks, s, ops, scratch, chunks, block_op);
+      else rotate_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
       break;
     default:
       if (use_tc) rotate_tc_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
-      else rotate_launch<32>(nblocks, s, ops, scratch, chunks, block_op);
+      else rotate_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
       break;
   }
   return cudaGetLastError();
@@ -89,7 +100,7 @@ __global__ void k_pool_complete(const PoolOp* __restrict__ ops, int count, PoolC
   c.stream = op.sid;
   c.kind = op.kind;
   const int status = st->status;
-  c.status = status & kStNonFinite ? 9 : status & kStNotConv ? 6 : status & kStTimeout ? 7 : 0;  // isvd_status
+  c.status = status & kStNonFinite ? 9 : status & kStNotConv ? 6 : status & kStTimeout ? 7 : status & kStLayout ? 8 : 0;  // isvd_status
   c.r = st->r;
   c.rho = op.kind == kEntry ? 0.0 : st->rho;
   c.sigma_max = st->r > 0 ? op.sig[0] : 0.0;
@@ -104,6 +115,10 @@ __global__ void k_pool_gather_sigma(const double* const* __restrict__ sig, const
   const int64_t s = idx / ld;
   const int c = (int)(idx - s * ld);
   out[idx] = c < st[s]->r ? sig[s][c] : 0.0;
+}
+__global__ void k_pool_gather_status(const DevState* const* __restrict__ st, int64_t n, int* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[s] = st[s]->status;
 }
 // Adaptive rank (Eq. evr-rank-rule as a growth rule), one thread per listed stream.
 __global__ void k_pool_rank(const PoolRankOp* __restrict__ list, int count, double tau) {
@@ -139,11 +154,17 @@ cudaError_t pool_gather_sigma_launch(int64_t n, cudaStream_t s, const double* co
   return cudaGetLastError();
 }
 
+cudaError_t pool_gather_status_launch(int64_t n, cudaStream_t s, const DevState* const* st, int* out) {
+  if (n <= 0) return cudaSuccess;
+  k_pool_gather_status<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(st, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t pool_warp_set_attrs() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_pool_rotate<32>, a, (int)rot_smem_bytes<32>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_rotate<16>, a, (int)rot_smem_bytes<16>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_rotate<8>, a, (int)rot_smem_bytes<8>());
+  cudaError_t e = cudaFuncSetAttribute(k_pool_rotate<32>, a, (int)RotTmaLayout<32>::kBytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_rotate<16>, a, (int)RotTmaLayout<16>::kBytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_rotate<8>, a, (int)RotTmaLayout<8>::kBytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_warp<8>, a, (int)warp_block_smem<8>());
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_warp<16>, a, (int)warp_block_smem<16>());
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pool_warp<32>, a, (int)warp_block_smem<32>());

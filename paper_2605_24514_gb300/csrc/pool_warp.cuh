@@ -22,9 +22,9 @@
 //               values sqrt(lambda) in FP64
 //   rotations   P' = [P z_hat] V_K with z_hat = (x - P p) / rho recomputed per row in float-float,
 //               Q' = blkdiag(Q, 1) U_K (the new row of Q' is U_K's last row): a separate
-//               row-parallel launch (k_pool_rotate, one thread per row) reading V_K, U_K and p
-//               from a per-update scratch record, since one warp cannot hide the latency of
-//               rotating hundreds of rows.
+//               row-parallel launch (k_pool_rotate in pool_rotate_tma.cuh, two rows per
+//               thread) reading V_K, U_K and p from a per-update scratch record, since one warp
+//               cannot hide the latency of rotating hundreds of rows.
 // An update the warp cannot finish on this path (non-finite input, coinciding poles, a deflated
 // rho pole, a rejected weight correction, an empty factorisation) changes nothing and is listed
 // for the CTA kernel (k_pool_retry), which has the Jacobi fallback.
@@ -71,23 +71,6 @@ struct alignas(16) RotScratch {
 };
 constexpr size_t kRotScratchStride = sizeof(RotScratch<kWarpKB>);  // bytes per update slot
 
-// r leading entries of a row (16-byte aligned, row stride a multiple of 4 floats), zero beyond.
-template <int KB>
-__device__ __forceinline__ void warp_load_row(const float* p, int r, float (&v)[KB]) {
-#pragma unroll
-  for (int c4 = 0; c4 < KB; c4 += 4) {
-    if (c4 < r) {
-      const float4 q = *reinterpret_cast<const float4*>(p + c4);
-      v[c4] = q.x;
-      v[c4 + 1] = c4 + 1 < r ? q.y : 0.f;
-      v[c4 + 2] = c4 + 2 < r ? q.z : 0.f;
-      v[c4 + 3] = c4 + 3 < r ? q.w : 0.f;
-    } else {
-      v[c4] = v[c4 + 1] = v[c4 + 2] = v[c4 + 3] = 0.f;
-    }
-  }
-}
-
 // Warp-wide sums of KB per-lane vectors: returns, on lane L, sum over lanes of v[L % KB]. The
 // first log2(KB) rounds exchange half of the remaining entries with the partner lane (a register
 // transpose, KB - 1 shuffles), the rest add across lane groups.
@@ -107,108 +90,6 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[KB], int lane) {
 #pragma unroll
   for (int o = KB; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
-}
-
-// out[jj] = sum_{c < r} xv[c] R[c][jj] (+ zh R[r][jj]) for jj < k_out (R row stride KB), written
-// back to row y, eight output columns per pass (the pass loop stays rolled: compact code).
-template <int KB>
-__device__ __forceinline__ void warp_rotate_row(float* y, const float (&xv)[KB], int r, const float* R, int k_out,
-                                                float zh, bool withz) {
-#pragma unroll 1
-  for (int h0 = 0; h0 < k_out; h0 += 8) {
-    float o[8];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) o[jj] = 0.f;
-#pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      if (c < r) {
-        const float4* rr = reinterpret_cast<const float4*>(R + c * KB + h0);
-        const float4 a = rr[0], b = rr[1];
-        o[0] = fmaf(xv[c], a.x, o[0]);
-        o[1] = fmaf(xv[c], a.y, o[1]);
-        o[2] = fmaf(xv[c], a.z, o[2]);
-        o[3] = fmaf(xv[c], a.w, o[3]);
-        o[4] = fmaf(xv[c], b.x, o[4]);
-        o[5] = fmaf(xv[c], b.y, o[5]);
-        o[6] = fmaf(xv[c], b.z, o[6]);
-        o[7] = fmaf(xv[c], b.w, o[7]);
-      }
-    }
-    if (withz) {
-      const float4* rr = reinterpret_cast<const float4*>(R + r * KB + h0);
-      const float4 a = rr[0], b = rr[1];
-      o[0] = fmaf(zh, a.x, o[0]);
-      o[1] = fmaf(zh, a.y, o[1]);
-      o[2] = fmaf(zh, a.z, o[2]);
-      o[3] = fmaf(zh, a.w, o[3]);
-      o[4] = fmaf(zh, b.x, o[4]);
-      o[5] = fmaf(zh, b.y, o[5]);
-      o[6] = fmaf(zh, b.z, o[6]);
-      o[7] = fmaf(zh, b.w, o[7]);
-    }
-    if (h0 + 7 < k_out) {
-      *reinterpret_cast<float4*>(y + h0) = make_float4(o[0], o[1], o[2], o[3]);
-      *reinterpret_cast<float4*>(y + h0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj)
-        if (h0 + jj < k_out) y[h0 + jj] = o[jj];
-    }
-  }
-}
-
-// Two rows at once (y1 only when has1): every U_K / V_K value read from shared memory feeds both
-// rows, which halves the shared-memory traffic per FMA (the rotation kernel's bound otherwise).
-template <int KB>
-__device__ __forceinline__ void rotate_two_rows(float* y0, float* y1, const float (&x0)[KB], const float (&x1)[KB],
-                                                int r, const float* R, int k_out, float z0, float z1, bool withz,
-                                                bool has1) {
-#pragma unroll 1
-  for (int h0 = 0; h0 < k_out; h0 += 8) {
-    float o0[8], o1[8];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) o0[jj] = o1[jj] = 0.f;
-#pragma unroll
-    for (int c = 0; c <= KB; ++c) {
-      if (c < r || (c == r && withz)) {
-        const float4* rr = reinterpret_cast<const float4*>(R + c * KB + h0);
-        const float4 a = rr[0], b = rr[1];
-        const float u0 = c < r ? x0[c < KB ? c : 0] : z0;
-        const float u1 = c < r ? x1[c < KB ? c : 0] : z1;
-        o0[0] = fmaf(u0, a.x, o0[0]);
-        o0[1] = fmaf(u0, a.y, o0[1]);
-        o0[2] = fmaf(u0, a.z, o0[2]);
-        o0[3] = fmaf(u0, a.w, o0[3]);
-        o0[4] = fmaf(u0, b.x, o0[4]);
-        o0[5] = fmaf(u0, b.y, o0[5]);
-        o0[6] = fmaf(u0, b.z, o0[6]);
-        o0[7] = fmaf(u0, b.w, o0[7]);
-        o1[0] = fmaf(u1, a.x, o1[0]);
-        o1[1] = fmaf(u1, a.y, o1[1]);
-        o1[2] = fmaf(u1, a.z, o1[2]);
-        o1[3] = fmaf(u1, a.w, o1[3]);
-        o1[4] = fmaf(u1, b.x, o1[4]);
-        o1[5] = fmaf(u1, b.y, o1[5]);
-        o1[6] = fmaf(u1, b.z, o1[6]);
-        o1[7] = fmaf(u1, b.w, o1[7]);
-      }
-    }
-    if (h0 + 7 < k_out) {
-      *reinterpret_cast<float4*>(y0 + h0) = make_float4(o0[0], o0[1], o0[2], o0[3]);
-      *reinterpret_cast<float4*>(y0 + h0 + 4) = make_float4(o0[4], o0[5], o0[6], o0[7]);
-      if (has1) {
-        *reinterpret_cast<float4*>(y1 + h0) = make_float4(o1[0], o1[1], o1[2], o1[3]);
-        *reinterpret_cast<float4*>(y1 + h0 + 4) = make_float4(o1[4], o1[5], o1[6], o1[7]);
-      }
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj)
-        if (h0 + jj < k_out) {
-          y0[h0 + jj] = o0[jj];
-          if (has1) y1[h0 + jj] = o1[jj];
-        }
-    }
-  }
 }
 
 // Next non-deflated pole above j (bit set in mask), or -1.
@@ -564,10 +445,12 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   __syncwarp();
 
   ISVD_WSTAMP(22, tp);
-  // Hand V_K, U_K and p to the rotation kernel; the new row of Q is U_K's last row.
-  for (int idx = lane; idx < (r + 1) * KB; idx += 32) {
-    RS.RP[idx] = S.RP[idx];
-    RS.RQ[idx] = S.RQ[idx];
+  // Hand V_K, U_K and p to the rotation kernel (rows beyond r zero: it sums over all KB rows);
+  // the new row of Q is U_K's last row.
+  for (int idx = lane; idx < (KB + 1) * KB; idx += 32) {
+    const bool in = idx < (r + 1) * KB;
+    RS.RP[idx] = in ? S.RP[idx] : 0.f;
+    RS.RQ[idx] = in ? S.RQ[idx] : 0.f;
   }
   for (int c = lane; c < r; c += 32) {
     RS.ph[c] = S.ph[c];
@@ -627,94 +510,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
   if (!ok && (threadIdx.x & 31) == 0) {
     scratch[e].k_out = -1;
     retry[atomicAdd(retry_n, 1)] = base + e;
-  }
-}
-
-// Rotations of the warp kernel's updates: block b rotates kPoolRotRows rows of one side of update
-// e = block_op[b] (chunk_start[e] = its first block; per update ceil(nP / kPoolRotRows) blocks for
-// the projection side, then ceil(nQ / kPoolRotRows) for the other). Rows are KB floats wide and
-// contiguous, so the block's rows form one contiguous tile: it is read and written with coalesced
-// float4 accesses through a padded shared-memory copy (row stride KB + 4 floats, conflict-free
-// for a thread reading its own row), and each thread rotates two rows from there.
-constexpr int kRotPad = 4;
-template <int KB>
-constexpr size_t rot_smem_bytes() {
-  return ((size_t)kPoolRotRows * (KB + kRotPad) + (size_t)(KB + 1) * KB + 2 * KB) * sizeof(float);
-}
-template <int KB>
-__global__ void __launch_bounds__(kPoolRotThreads, KB <= 16 ? 6 : 4)
-    k_pool_rotate(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
-                  const int* __restrict__ chunk_start, const int* __restrict__ block_op) {
-  extern __shared__ __align__(16) float rsm[];
-  constexpr int LS = KB + kRotPad;  // padded row stride of the tile
-  constexpr int C4 = KB / 4;        // float4 chunks per row
-  float* T = rsm;                   // kPoolRotRows x LS
-  float* R = T + kPoolRotRows * LS;  // (KB + 1) x KB
-  float* ph = R + (KB + 1) * KB;
-  float* pl = ph + KB;
-  const int b = blockIdx.x;
-  const int e = block_op[b];
-  const RotScratch<KB>& sc = scratch[e];
-  const int k_out = sc.k_out;
-  if (k_out < 0) return;
-  const PoolOp& op = ops[e];
-  const bool is_row = op.kind == kRow;
-  const int64_t nP = is_row ? op.n : op.m;
-  const int64_t nQ = is_row ? op.m : op.n;
-  const int cP = (int)((nP + kPoolRotRows - 1) / kPoolRotRows);
-  const int ci = b - chunk_start[e];
-  const bool pside = ci < cP;
-  const int r = sc.r;
-  const bool withz = pside && sc.grew;
-  const int64_t nrows = pside ? nP : nQ;
-  const int64_t base = (int64_t)(pside ? ci : ci - cP) * kPoolRotRows;
-  const int rows = (int)(nrows - base < kPoolRotRows ? nrows - base : kPoolRotRows);
-  float* X = pside ? (is_row ? op.V : op.U) : (is_row ? op.U : op.V);
-  float4* X4 = reinterpret_cast<float4*>(X + base * KB);
-  const float* src = pside ? sc.RP : sc.RQ;
-  for (int idx = threadIdx.x; idx < (r + 1) * KB; idx += kPoolRotThreads) R[idx] = src[idx];
-  if (withz)
-    for (int c = threadIdx.x; c < r; c += kPoolRotThreads) {
-      ph[c] = sc.ph[c];
-      pl[c] = sc.pl[c];
-    }
-  for (int f = threadIdx.x; f < rows * C4; f += kPoolRotThreads) {
-    const int rr = f / C4, q = f - rr * C4;
-    *reinterpret_cast<float4*>(T + rr * LS + 4 * q) = X4[f];
-  }
-  __syncthreads();
-  const int t0 = threadIdx.x, t1 = threadIdx.x + kPoolRotThreads;
-  if (t0 < rows) {
-    const bool has1 = t1 < rows;
-    float* y0 = T + t0 * LS;
-    float* y1 = T + (has1 ? t1 : t0) * LS;
-    float x0[KB], x1[KB];
-    warp_load_row<KB>(y0, r, x0);
-    warp_load_row<KB>(y1, r, x1);
-    float z0 = 0.f, z1 = 0.f;
-    if (withz) {
-      ff s0{op.x[base + t0], 0.f}, s1{op.x[base + (has1 ? t1 : t0)], 0.f};
-#pragma unroll
-      for (int c = 0; c < KB; ++c) {
-        if (c < r) {
-          ff q = two_prod(x0[c], ph[c]);
-          q.lo = fmaf(x0[c], pl[c], q.lo);
-          s0 = ff_add(s0, ff{-q.hi, -q.lo});
-          q = two_prod(x1[c], ph[c]);
-          q.lo = fmaf(x1[c], pl[c], q.lo);
-          s1 = ff_add(s1, ff{-q.hi, -q.lo});
-        }
-      }
-      z0 = (s0.hi + s0.lo) * sc.inv_rho;
-      z1 = (s1.hi + s1.lo) * sc.inv_rho;
-    }
-    rotate_two_rows<KB>(y0, y1, x0, x1, r, R, k_out, z0, z1, withz, has1);
-  }
-  __syncthreads();
-  // Columns >= k_out keep whatever the tile held (stale, never read: the working rank is k_out).
-  for (int f = threadIdx.x; f < rows * C4; f += kPoolRotThreads) {
-    const int rr = f / C4, q = f - rr * C4;
-    X4[f] = *reinterpret_cast<const float4*>(T + rr * LS + 4 * q);
   }
 }
 

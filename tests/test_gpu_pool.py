@@ -279,14 +279,14 @@ def test_pool_warp_ranks_and_sides(isvd, k):
 
 @pytest.mark.parametrize("k", [9, 16, 21, 32])
 def test_pool_tensor_core_rotation_matches_fp32_pipes(isvd, k):
-    """The tensor-core rotation (split-TF32 operands, rank buckets 16 and 32) against the FP32-pipe
-    rotation and the oracle, on sides that span several 256-row tiles with ragged tails (rows and
+    """The tensor-core rotation (exact BF16 digit products, rank buckets 16 and 32) against the
+    FP32-pipe rotation and the oracle, on sides that span several 256-row tiles with ragged tails (rows and
     columns interleaved, so both the projection side with z_hat and the other side are rotated)."""
     A0, fm = streams.make_panel(613, 301, 40, seed=60 + k)
     A0 = A0.astype(np.float32)
     f = oracle.truncated_svd(A0.astype(np.float64), k)
     ev = streams.make_events(fm, 613, 10, mix=(0.6, 0.4, 0.0), seed=80 + k)
-    pools = [isvd.Pool(k_max=32), isvd.Pool(k_max=32, flags=isvd.POOL_SIMT_ROTATIONS)]
+    pools = [isvd.Pool(k_max=32, flags=isvd.POOL_TC_ROTATIONS), isvd.Pool(k_max=32)]
     sids = [p.admit(A0, k, factors=f) for p in pools]
     o = oracle.OracleISVD(A0.astype(np.float64), k, tol_rel=3e-6, factors=f)
     for e in range(len(ev)):
@@ -364,3 +364,44 @@ def test_pool_completion_records_and_sigma_gather(isvd):
     assert e.value.name == "EINVAL"
     plain.close()
     pool.close()
+
+
+def test_pool_device_checks_report_nonfinite_per_stream(isvd):
+    """With POOL_DEVICE_CHECKS a host payload is not scanned on the host: a NaN in one stream's row
+    is caught by the kernels and reported for that stream alone (sticky ENONFINITE at sync, status
+    9 in its completion record), while the other streams' updates are exactly those of a pool that
+    never saw the bad op. Without the flag the same submit is refused up front, nothing queued."""
+    data = make_streams(4, seed=33, n_events=1, mix=(1.0, 0.0, 0.0), ks=(8, 16, 32, 32), nrange=(40, 90))
+    pools = [isvd.Pool(k_max=32, flags=isvd.POOL_COMPLETIONS | isvd.POOL_DEVICE_CHECKS),
+             isvd.Pool(k_max=32, flags=isvd.POOL_COMPLETIONS)]
+    ids = [[p.admit(A0, k) for A0, _, k in data] for p in pools]
+    rows = [ev.vector(0).astype(np.float32) for _, ev, _ in data]
+    bad = 2
+    rows_bad = [r.copy() for r in rows]
+    rows_bad[bad][3] = np.nan
+    offs = np.cumsum([0] + [r.size for r in rows])
+    ops = [(ids[0][s], streams.ROW, 0, 0, 0.0, int(offs[s]), rows[s].size) for s in range(len(rows))]
+    pools[0].submit(ops, np.concatenate(rows_bad))
+    with pytest.raises(isvd.IsvdError) as e:
+        pools[1].submit([(ids[1][s], *o[1:]) for s, o in enumerate(ops)], np.concatenate(rows_bad))
+    assert e.value.name == "ENONFINITE"
+    good = [s for s in range(len(rows)) if s != bad]
+    pay = np.concatenate([rows[s] for s in good])
+    goffs = np.cumsum([0] + [rows[s].size for s in good])
+    pools[1].submit([(ids[1][s], streams.ROW, 0, 0, 0.0, int(goffs[q]), rows[s].size) for q, s in enumerate(good)], pay)
+    with pytest.raises(isvd.IsvdError) as e:
+        pools[0].sync()
+    assert e.value.name == "ENONFINITE"
+    pools[1].sync()
+    rec = pools[0].poll()
+    assert rec.size == len(rows)
+    status = {int(r["stream"]): int(r["status"]) for r in rec}
+    assert status[ids[0][bad]] == 9 and all(status[ids[0][s]] == 0 for s in good)
+    for s in good:
+        a, b = pools[0].stream(ids[0][s]).factors(), pools[1].stream(ids[1][s]).factors()
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    pools[0].release(ids[0][bad])
+    pools[0].sync()                                   # the failure stayed with the released stream
+    for p in pools:
+        p.close()
