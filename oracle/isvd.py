@@ -15,7 +15,9 @@ Every routine follows the paper's steps in its own order and notation:
 * principal angles ........................... Section 2.4, Eqs. (theta-max), (angle-metrics-ref/opt)
 * Frobenius errors, ratio, EVR, N_t .......... Section 2.5, Eqs. (frob-errors), (frob-ratio), (evr)
 * refresh and rank policies .................. Section 3, Eqs. (periodic-refresh-rule),
-                                               (error-refresh-rule), angle rule, (evr-rank-rule)
+                                               (error-refresh-rule), angle rule, (evr-rank-rule),
+                                               (novelty-rank-rule)
+* successive-subspace angles ................. Section 3.3 ("subspace-change per update")
 
 Readings taken where the paper is silent or ambiguous are stated inline (marked
 "Reading:"); the same list appears in the design notes of the repository.
@@ -35,6 +37,7 @@ POLICY_PERIODIC = 1
 POLICY_ERROR = 2
 POLICY_ANGLE = 4
 POLICY_ADAPTIVE_RANK = 8
+POLICY_NOVELTY_RANK = 16
 
 
 # ---------------------------------------------------------------------------
@@ -161,6 +164,7 @@ class Policy:
     k_min: int = 1
     k_max: int = 0
     store_initial_subspace: bool = False
+    eta: float = 0.5
 
 
 @dataclass
@@ -176,6 +180,8 @@ class Metrics:
     angle: float = float("nan")
     angle_to_opt: float = float("nan")
     evr: float = float("nan")
+    angle_succ_u: float = float("nan")
+    angle_succ_v: float = float("nan")
     refreshed: bool = False
 
 
@@ -239,6 +245,8 @@ class OracleISVD:
         self.refreshes = 0
         self.rho_last = float("nan")
         self.novelty_last = float("nan")
+        self.angle_succ_u = float("nan")   # largest principal angle between span(U_{t-1}) and span(U_t)
+        self.angle_succ_v = float("nan")
         self.log: list[Metrics] = []
 
     # -- shape helpers ------------------------------------------------------
@@ -267,10 +275,13 @@ class OracleISVD:
         self.A.append_row(x)                              # append x^T to A
         self.N += float(x @ x)                            # N_{t+1} = N_t + ||x||^2
         U, s, V, rho, p, _ = row_append_update(self.U, self.s, self.V, x, self.tol_rel)
+        U0, V0 = self.U, self.V
         self.U, self.s, self.V = truncate(U, s, V, self.k)
+        self._successive_angles(U0, V0)
         self.rho_last = rho
         nx = float(np.linalg.norm(x))
         self.novelty_last = rho / nx if nx > 0 else 0.0   # ||z|| / ||x|| (Section 3.3)
+        self._novelty_rule(rho, nx)
         self._after_update()
 
     def append_col(self, y):
@@ -279,10 +290,13 @@ class OracleISVD:
         self.A.append_col(y)                              # append y as right-most column
         self.N += float(y @ y)                            # N_{t+1} = N_t + ||y||^2
         U, s, V, rho, p, _ = col_append_update(self.U, self.s, self.V, y, self.tol_rel)
+        U0, V0 = self.U, self.V
         self.U, self.s, self.V = truncate(U, s, V, self.k)
+        self._successive_angles(U0, V0)
         self.rho_last = rho
         ny = float(np.linalg.norm(y))
         self.novelty_last = rho / ny if ny > 0 else 0.0
+        self._novelty_rule(rho, ny)
         self._after_update()
 
     def update_entry(self, i, j, delta):
@@ -293,7 +307,9 @@ class OracleISVD:
         self.N += 2.0 * delta * a_ij + delta * delta      # N_{t+1} = N_t + 2 delta A_ij + delta^2
         Av[i, j] = a_ij + delta                           # A_ij <- A_ij + delta
         U, s, V = rank_one_update(self.U, self.s, self.V, i, j, delta)
+        U0, V0 = self.U, self.V
         self.U, self.s, self.V = truncate(U, s, V, self.k)
+        self._successive_angles(U0, V0)
         self._after_update()
 
     def apply(self, kind, vec=None, i=0, j=0, delta=0.0):
@@ -351,8 +367,26 @@ class OracleISVD:
                      frob_gap=E_inc - E_opt, frob_ratio=ratio,
                      angle=theta_max(self.U_ref, self.U),
                      angle_to_opt=theta_max(U_opt, self.U),
-                     evr=float(np.sum(self.s ** 2) / self.N) if self.N > 0 else float("nan"))
+                     evr=float(np.sum(self.s ** 2) / self.N) if self.N > 0 else float("nan"),
+                     angle_succ_u=self.angle_succ_u, angle_succ_v=self.angle_succ_v)
         return mt
+
+    def _successive_angles(self, U0, V0):
+        """Section 3.3, "subspace-change per update": the largest principal angle between the
+        subspaces before and after the update, Eq. (theta-max) applied to (U_{t-1}, U_t) and to
+        (V_{t-1}, V_t). Reading: an appended row (column) extends the previous basis by a zero
+        row, as for the angle to the stored basis; with bases of different ranks the angle is
+        taken over the min(r_{t-1}, r_t) principal angles (zero when one span contains the other)."""
+        self.angle_succ_u = theta_max(U0, self.U)
+        self.angle_succ_v = theta_max(V0, self.V)
+
+    def _novelty_rule(self, rho, xnorm):
+        """Eq. (novelty-rank-rule): ||z_t|| > eta ||x_t||  =>  k_{t+1} <- min(k_t + 1, k_max).
+        Reading: the rule acts after the append (the append itself is truncated at k_t), for row
+        and column appends alike, and the grown rank takes effect at the next update."""
+        pol = self.policy
+        if pol.kind & POLICY_NOVELTY_RANK and rho > pol.eta * xnorm:
+            self.k = min(self.k + 1, pol.k_max if pol.k_max > 0 else self.k + 1)
 
     def _after_update(self):
         """t <- t + 1, then the refresh rule pi(t, metrics) (Algorithm 1)."""
