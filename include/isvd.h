@@ -80,6 +80,9 @@ typedef struct {
 #define ISVD_POLICY_ANGLE 4          /* refresh iff angle_to_opt > theta_max (Section 3.3) */
 #define ISVD_POLICY_ADAPTIVE_RANK 8  /* k <- min(k + 1, k_max) while EVR < tau_evr at a check,
                                         Eq. (evr-rank-rule) read as a growth rule */
+#define ISVD_POLICY_NOVELTY_RANK 16  /* after a row or column append with rho > eta ||x||,
+                                        k <- min(k + 1, k_max) for the next update, Eq.
+                                        (novelty-rank-rule); decided on the device */
 
 typedef struct {
   int32_t kind;                    /* bit set of ISVD_POLICY_* */
@@ -91,6 +94,7 @@ typedef struct {
   double gamma;                    /* error-ratio threshold */
   double theta_max_rad;            /* angle threshold in radians */
   double tau_evr;                  /* EVR target */
+  double eta;                      /* novelty threshold in (0, 1) (ISVD_POLICY_NOVELTY_RANK) */
 } isvd_policy;
 
 /* Metrics of Section 2.5 (names follow the paper). */
@@ -115,6 +119,10 @@ typedef struct {
   int32_t core_sweeps;   /* last core SVD: Jacobi sweeps (-1: not converged), or 100 + i for the secular
                             core (i = 0, 1: Gram-verified after i refinements; 2: corrected weights) */
   int32_t reserved0;
+  double angle_succ_u;   /* largest principal angle between span(U_{t-1}) and span(U_t) (Section 3.3,
+                            subspace change per update; an appended row extends U_{t-1} by a zero
+                            row); 0 for an entry update, NaN before the first update */
+  double angle_succ_v;   /* the same for V */
 } isvd_metrics_t;
 
 /* Flags of isvd_metrics. */
@@ -260,6 +268,9 @@ typedef struct {
                                 residual. 0: off. The capacity is the stream's rank bucket (8, 16,
                                 32, 64 or 128, the smallest holding the admitted k) capped by k_max. */
   double tau_evr;            /* EVR target of the adaptive rank rule */
+  double eta_novelty;        /* novelty rank rule for every stream (Eq. novelty-rank-rule): after an
+                                append with rho > eta_novelty ||x||, k <- min(k + 1, capacity) for
+                                the stream's next update; 0: off, else in (0, 1) */
 } isvd_pool_config;
 
 /* isvd_pool_config.flags */

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libisvd.so")
 FP64, FP32 = 0, 1
 ROW, COL, ENTRY = 0, 1, 2
 POLICY_NONE, POLICY_PERIODIC, POLICY_ERROR, POLICY_ANGLE, POLICY_ADAPTIVE_RANK = 0, 1, 2, 4, 8
+POLICY_NOVELTY_RANK = 16
 METRICS_CHEAP, METRICS_FULL = 0, 1
 KCLASS = {"proj": 0, "core": 1, "rotate": 2, "check": 3, "refresh": 4, "reorth": 5}
 
@@ -44,7 +45,7 @@ class Policy(C.Structure):
     _fields_ = [("kind", C.c_int32), ("k_min", C.c_int32), ("k_max", C.c_int32),
                 ("store_initial_subspace", C.c_int32), ("T_refresh", C.c_int64), ("T_min", C.c_int64),
                 ("check_every", C.c_int64), ("gamma", C.c_double), ("theta_max_rad", C.c_double),
-                ("tau_evr", C.c_double)]
+                ("tau_evr", C.c_double), ("eta", C.c_double)]
 
 
 class Metrics(C.Structure):
@@ -54,7 +55,8 @@ class Metrics(C.Structure):
                 ("evr", C.c_double), ("rho_last", C.c_double), ("novelty_last", C.c_double),
                 ("orth_err_u", C.c_double), ("orth_err_v", C.c_double), ("N", C.c_double),
                 ("refreshes", C.c_int64), ("reorths", C.c_int64), ("t_last", C.c_int64),
-                ("core_sweeps", C.c_int32), ("reserved0", C.c_int32)]
+                ("core_sweeps", C.c_int32), ("reserved0", C.c_int32),
+                ("angle_succ_u", C.c_double), ("angle_succ_v", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,7 +66,7 @@ class PoolConfig(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("flags", C.c_int32), ("max_streams", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double),
                 ("orth_every", C.c_int64), ("orth_tol", C.c_double), ("rank_every", C.c_int64),
-                ("tau_evr", C.c_double)]
+                ("tau_evr", C.c_double), ("eta_novelty", C.c_double)]
 
 
 POOL_TC_ROTATIONS = 1
@@ -256,10 +258,10 @@ class ISVD:
         self._check(lib().isvd_apply_events(self._h, arr, n, p, plen, d), "apply_events")
 
     def set_policy(self, kind=POLICY_NONE, T_refresh=0, T_min=0, check_every=0, gamma=1.1,
-                   theta_max=np.pi / 2, tau_evr=0.9, k_min=1, k_max=0, store_initial_subspace=False):
+                   theta_max=np.pi / 2, tau_evr=0.9, k_min=1, k_max=0, store_initial_subspace=False, eta=0.5):
         pol = Policy(kind=kind, k_min=k_min, k_max=k_max, store_initial_subspace=int(store_initial_subspace),
                      T_refresh=T_refresh, T_min=T_min, check_every=check_every, gamma=gamma,
-                     theta_max_rad=theta_max, tau_evr=tau_evr)
+                     theta_max_rad=theta_max, tau_evr=tau_evr, eta=eta)
         self._check(lib().isvd_set_policy(self._h, C.byref(pol)), "set_policy")
 
     def refresh(self, store_initial_subspace=False):
@@ -435,10 +437,10 @@ class Pool:
     """Many independent FP32 streams updated by fused per-tick launches (isvd_pool_*)."""
 
     def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0, flags=0,
-                 orth_every=0, orth_tol=0.0, rank_every=0, tau_evr=0.9):
+                 orth_every=0, orth_tol=0.0, rank_every=0, tau_evr=0.9, eta_novelty=0.0):
         cfg = PoolConfig(k_max=k_max, flags=flags, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
                          cuda_stream=stream or 0, tol_rel=tol_rel, orth_every=orth_every, orth_tol=orth_tol,
-                         rank_every=rank_every, tau_evr=tau_evr)
+                         rank_every=rank_every, tau_evr=tau_evr, eta_novelty=eta_novelty)
         h = C.c_void_p()
         st = lib().isvd_pool_create(C.byref(cfg), C.byref(h))
         if st:

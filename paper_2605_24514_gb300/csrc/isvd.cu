@@ -767,8 +767,8 @@ isvd_status store_ref(isvd_ctx* h, int r) {
 template <typename T>
 isvd_status do_refresh(isvd_ctx* h, int store) {
   isvd_status s;
-  if (h->orth_on_device) {
-    // A pool stream's working rank may have been grown on the device by the batched rank rule.
+  {
+    // The working rank may have been grown on the device (novelty rule, the pool's rank rule).
     DevState ds;
     if ((s = read_state(h, &ds))) return s;
     h->k_host = ds.k;
@@ -841,6 +841,8 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   mt->evr = ds.N > 0 ? ss / ds.N : NAN;
   mt->rho_last = ds.rho;
   mt->novelty_last = ds.novelty;
+  mt->angle_succ_u = ds.ang_u;
+  mt->angle_succ_v = ds.ang_v;
   mt->orth_err_u = h->orth_on_device && ds.orth_runs > 0 ? ds.orth_u : h->orth_err_u;
   mt->orth_err_v = h->orth_on_device && ds.orth_runs > 0 ? ds.orth_v : h->orth_err_v;
   mt->refreshes = h->refreshes;
@@ -1038,6 +1040,7 @@ isvd_status after_update(isvd_ctx* h) {
       if ((pol.kind & ISVD_POLICY_ANGLE) && spaced && std::isfinite(mt.angle_to_opt) &&
           mt.angle_to_opt > pol.theta_max_rad)
         fire = true;
+      h->k_host = mt.k;  // the device's working rank (the novelty rule may have grown it)
       if ((pol.kind & ISVD_POLICY_ADAPTIVE_RANK) && std::isfinite(mt.evr) && mt.evr < pol.tau_evr) {
         const int kcap = pol.k_max > 0 ? std::min(pol.k_max, h->kmax) : h->kmax;
         const int knew = std::min(h->k_host + 1, kcap);
@@ -1113,6 +1116,7 @@ isvd_status create_impl(isvd_ctx* h, const void* A0, int64_t m0, int64_t n0, int
   // N_0 = ||A0||_F^2 (Section 2.4): the trace of the Gram of A0 through the same product kernel.
   DevState ds{};
   ds.k = k;
+  ds.ang_u = ds.ang_v = NAN;  // no update yet
   CK(h, cudaMemcpyAsync(h->st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemsetAsync(h->scal, 0, 64, h->stream));
   {
@@ -1302,11 +1306,27 @@ isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const
 isvd_status isvd_set_policy(isvd_t h, const isvd_policy* pol) {
   if (!h) return ISVD_EINVAL;
   if (!pol) {
+    if (h->has_pol && (h->pol.kind & ISVD_POLICY_NOVELTY_RANK)) {
+      const int32_t off = 0;
+      CK(h, cudaMemcpyAsync(&h->st->kcap_nov, &off, sizeof off, cudaMemcpyHostToDevice, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+    }
     h->has_pol = 0;
     return ISVD_OK;
   }
   if (pol->T_refresh < 0 || pol->T_min < 0 || pol->check_every < 0) return ISVD_EINVAL;
+  if (pol->kind & ~(ISVD_POLICY_PERIODIC | ISVD_POLICY_ERROR | ISVD_POLICY_ANGLE | ISVD_POLICY_ADAPTIVE_RANK |
+                    ISVD_POLICY_NOVELTY_RANK))
+    return fail(h, ISVD_EINVAL, "unknown policy kind bit");
   if (pol->k_max > h->kmax) return fail(h, ISVD_EINVAL, "policy k_max exceeds the handle's k_max");
+  const bool nov = (pol->kind & ISVD_POLICY_NOVELTY_RANK) != 0;
+  if (nov && !(pol->eta > 0.0 && pol->eta < 1.0)) return fail(h, ISVD_EINVAL, "novelty threshold eta not in (0, 1)");
+  // The novelty rule is decided on the device, right after each append's core.
+  const double eta = nov ? pol->eta : 0.0;
+  const int32_t kcap = nov ? (pol->k_max > 0 ? pol->k_max : h->kmax) : 0;
+  CK(h, cudaMemcpyAsync(&h->st->eta_nov, &eta, sizeof eta, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(&h->st->kcap_nov, &kcap, sizeof kcap, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
   h->pol = *pol;
   h->has_pol = 1;
   return ISVD_OK;
@@ -1477,6 +1497,8 @@ struct isvd_pool_ctx {
   int* status_dev = nullptr;   // every slot's status word (isvd_pool_sync), device and pinned host
   int* status_host = nullptr;
   int64_t status_cap = 0;
+  int* kcheck = nullptr;       // the pool kernels' self-check word: first failing check (code, detail)
+  int* kcheck_host = nullptr;  // its pinned copy, read at isvd_pool_sync
   // Tensor maps (CUtensorMap, 128 bytes) of every slot's U and V for the tensor-core rotations
   // (TMA loads of 128-row boxes, swizzled), rebuilt when a stream's U or V is reallocated.
   CUtensorMap* tmaps_dev = nullptr;
@@ -1490,6 +1512,7 @@ struct isvd_pool_ctx {
   // Adaptive rank (rank_every > 0): streams due after each tick of a submit.
   int64_t rank_every = 0;
   double tau_evr = 0.9;
+  double eta_nov = 0.0;  // novelty rank rule threshold (0: off)
   std::vector<PoolRankOp> v_rank;
   std::vector<int64_t> v_rank_start;
   PoolRankOp* rank_dev = nullptr;
@@ -1519,6 +1542,8 @@ struct isvd_pool_ctx {
   int stage_cur = 0;
   void* payload = nullptr;
   int64_t payload_cap = 0;
+  float* zbuf = nullptr;      // first-pass residuals of the appends' projection sides (PoolOp::z1)
+  int64_t zbuf_cap = 0;       // elements
   int* retry_list = nullptr;  // per-tick list of warp-path updates handed to the CTA kernel
   int64_t retry_cap = 0;
   int* retry_n = nullptr;     // one counter per tick of a submit
@@ -1603,11 +1628,11 @@ isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
 // listed as base + index into the tick's warp ops.
 template <int KB>
 isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, int base, int t,
-                             const int* chunks, int* block_op) {
+                             const int* chunks, int* block_op, int nblocks) {
   void* scr = static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
   cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op,
-                                   pool_rot_rows(KB, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0));
+                                   pool_rot_rows(KB, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0), nblocks, p->kcheck);
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1617,11 +1642,11 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
 // Row-parallel rotations of a bucket run (chunks = its first-block table, nblocks in total).
 template <int KB>
 isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int base, const int* chunks,
-                               const int* block_op, int nblocks) {
+                               const int* block_op, int nblocks, int count) {
   const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
   cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0,
-                                     p->tmaps_dev);
+                                     p->tmaps_dev, count, (int)(2 * p->tmaps_cap), p->kcheck);
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rotate launch: ") + cudaGetErrorString(e));
   p->launches++;
@@ -1756,6 +1781,7 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   *out = nullptr;
   if (cfg->k_max < 1 || cfg->k_max > kKmaxLimit) return ISVD_EINVAL;
   if (cfg->flags & ~(ISVD_POOL_TC_ROTATIONS | ISVD_POOL_COMPLETIONS | ISVD_POOL_DEVICE_CHECKS)) return ISVD_EINVAL;
+  if (!(cfg->eta_novelty == 0.0 || (cfg->eta_novelty > 0.0 && cfg->eta_novelty < 1.0))) return ISVD_EINVAL;
   isvd_pool_ctx* p = new isvd_pool_ctx();
   p->kmax = cfg->k_max;
   p->kb = kb_bucket(cfg->k_max);
@@ -1768,6 +1794,7 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->orth_tol = cfg->orth_tol > 0 ? cfg->orth_tol : 1e-5;
   p->rank_every = cfg->rank_every > 0 ? cfg->rank_every : 0;
   p->tau_evr = cfg->tau_evr;
+  p->eta_nov = cfg->eta_novelty;
   p->cfg.prec = ISVD_FP32;
   p->cfg.k_max = p->kmax;
   p->cfg.tol_rel = p->tol_rel;
@@ -1796,6 +1823,9 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->zero_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMemset(p->zero_sig, 0, 8 * (kKmaxLimit + 2));
   if (e == cudaSuccess) e = cudaMemset(p->zero_st, 0, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->kcheck, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->kcheck, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->kcheck_host, 2 * sizeof(int));
   if (e != cudaSuccess) {
     delete p;
     return ISVD_ECUDA;
@@ -1840,6 +1870,8 @@ void isvd_pool_destroy(isvd_pool_t p) {
   if (p->gather_dev) cudaFree(p->gather_dev);
   if (p->status_dev) cudaFree(p->status_dev);
   if (p->status_host) cudaFreeHost(p->status_host);
+  if (p->kcheck) cudaFree(p->kcheck);
+  if (p->kcheck_host) cudaFreeHost(p->kcheck_host);
   if (p->tmaps_dev) cudaFree(p->tmaps_dev);
   for (auto& sg : p->stage) {
     if (sg.ops) cudaFreeHost(sg.ops);
@@ -1849,6 +1881,7 @@ void isvd_pool_destroy(isvd_pool_t p) {
     if (sg.copied) cudaEventDestroy(sg.copied);
   }
   if (p->payload) cudaFree(p->payload);
+  if (p->zbuf) cudaFree(p->zbuf);
   delete p;
 }
 
@@ -1904,6 +1937,15 @@ isvd_status isvd_pool_admit(isvd_pool_t p, const void* A0, int64_t m0, int64_t n
   }
   p->s_gen[id] = 0;
   p->s_bucket[id] = (uint8_t)pool_bucket(k);
+  if (p->eta_nov > 0.0) {
+    // The novelty rank rule, decided on the device after each append, up to the stream's capacity.
+    const double eta = p->eta_nov;
+    const int32_t kcap = std::min<int32_t>(p->s_bucket[id], p->kmax);
+    if (cudaMemcpyAsync(&h->st->eta_nov, &eta, sizeof eta, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&h->st->kcap_nov, &kcap, sizeof kcap, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+      return pool_fail(p, ISVD_ECUDA, "pool novelty rule");
+  }
   p->used += need;
   *stream_id = id;
   return ISVD_OK;
@@ -2042,6 +2084,16 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       return pool_fail(p, ISVD_ECUDA, "pool payload copy");
     pay = (const float*)p->payload;
   }
+  if (payload_len > p->zbuf_cap) {
+    cudaStreamSynchronize(p->stream);
+    if (p->zbuf) cudaFree(p->zbuf);
+    p->zbuf = nullptr;
+    p->zbuf_cap = std::max(payload_len, 2 * p->zbuf_cap);
+    if (cudaMalloc((void**)&p->zbuf, sizeof(float) * (size_t)p->zbuf_cap) != cudaSuccess) {
+      p->zbuf_cap = 0;
+      return pool_fail(p, ISVD_ENOMEM, "pool residual buffer");
+    }
+  }
   const auto h1 = clk::now();
   // Order ops by tick (stable), build descriptors, then one descriptor copy for all ticks.
   std::vector<int64_t>& order = p->v_order;
@@ -2174,10 +2226,9 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       const int64_t e = order[q];
       const isvd_op& o = ops[e];
       isvd_ctx* h = p->streams[o.stream];
-      const int64_t prow = o.kind == kRow ? h->n : h->m;
       const int bk = p->s_bucket[o.stream];
       if (o.kind != kEntry && bk <= kWarpKB) fused[q] = 2;  // warp per update
-      else fused[q] = bk <= 64 && (o.kind == kEntry || prow <= kPoolZMax) ? 1 : 0;
+      else fused[q] = bk <= 64 ? 1 : 0;
       PoolOp& d = sg.ops[q];
       d.U = (float*)h->U;
       d.V = (float*)h->V;
@@ -2185,6 +2236,7 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       d.st = h->st;
       d.sig = h->sig;
       d.x = o.kind == kEntry ? nullptr : pay + o.off;
+      d.z1 = o.kind == kEntry ? nullptr : p->zbuf + o.off;
       d.m = h->m;
       d.n = h->n;
       d.lda = h->col_cap;
@@ -2366,16 +2418,16 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
           const int* ch = p->chunks_dev + b0;
           if (cudaStreamWaitEvent(cs, p->ev_fork, 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
           switch (bucket_of(b0)) {
-            case 8: s = pool_launch_warp<8>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
-            case 16: s = pool_launch_warp<16>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
-            default: s = pool_launch_warp<32>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop); break;
+            case 8: s = pool_launch_warp<8>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
+            case 16: s = pool_launch_warp<16>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
+            default: s = pool_launch_warp<32>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
           }
           if (s) return s;
           if (cudaEventRecord(p->ev_w[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
           switch (bucket_of(b0)) {
-            case 8: s = pool_launch_rotate<8>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
-            case 16: s = pool_launch_rotate<16>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
-            default: s = pool_launch_rotate<32>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0]); break;
+            case 8: s = pool_launch_rotate<8>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
+            case 16: s = pool_launch_rotate<16>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
+            default: s = pool_launch_rotate<32>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
           }
           if (s) return s;
           if (cudaEventRecord(p->ev_r[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
@@ -2496,6 +2548,8 @@ isvd_status isvd_pool_sync(isvd_pool_t p) {
       return pool_fail(p, ISVD_ENOMEM, "pool status words");
     }
   }
+  if (cudaMemcpyAsync(p->kcheck_host, p->kcheck, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return pool_fail(p, ISVD_ECUDA, "pool self-check copy");
   if (n > 0) {
     const cudaError_t e = pool_gather_status_launch(n, p->stream, p->tab_st, p->status_dev);
     if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool status gather: ") + cudaGetErrorString(e));
@@ -2505,6 +2559,9 @@ isvd_status isvd_pool_sync(isvd_pool_t p) {
       return pool_fail(p, ISVD_ECUDA, "pool status copy");
   }
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool sync");
+  if (p->kcheck_host[0] != 0)
+    return pool_fail(p, ISVD_ECUDA, "pool kernel self-check failed: code " + std::to_string(p->kcheck_host[0]) +
+                                        ", at " + std::to_string(p->kcheck_host[1]));
   for (int64_t i = 0; i < (int64_t)p->streams.size(); ++i) {
     isvd_ctx* h = p->streams[i];
     if (!h || (i < n && p->status_host[i] == 0)) continue;

@@ -45,7 +45,50 @@ struct DevState {
   double orth_v;
   int32_t reorths;
   int32_t orth_runs;
+  // Local angular signals of the last update (Section 3.3): the largest principal angle between
+  // span(U_{t-1}) and span(U_t), and between span(V_{t-1}) and span(V_t).
+  double ang_u;
+  double ang_v;
+  // Novelty rank rule (Eq. novelty-rank-rule): after an append with rho > eta_nov ||x||,
+  // k <- min(k + 1, kcap_nov) for the next update; kcap_nov = 0: off.
+  double eta_nov;
+  int32_t kcap_nov;
+  int32_t pad2;
 };
+
+// The successive-subspace angles of an append from its core factors, and the novelty rule.
+// QK: the factor of the side that gained the new row (U_K for a row append), PK: the side that
+// gained z_hat (V_K), both with row stride ld, row r the new row / z_hat's; the kept columns are
+// 0 .. k_out - 1. With [B; c^T] the kept block of an orthogonal factor (B its first r rows),
+// B^T B = I - c c^T, so the cosines of the principal angles between the old span (extended by a
+// zero row) and the new one are 1 but one, sqrt(1 - ||c||^2), when k_out <= r; when k_out > r the
+// old span lies inside the new one. The side that gained no direction keeps its span.
+// The sums and the arcsine run in the factors' own precision (T). append_signals_sums takes the
+// squared norms ||c||^2 of the two kept rows already summed (zero when k_out > r).
+template <typename T>
+__device__ inline void append_signals_sums(DevState* st, bool kind_row, T cq, T cp, bool grew, int kt) {
+  const T one = T(1);
+  const T aq = asin(sqrt(cq) < one ? sqrt(cq) : one), ap = grew ? asin(sqrt(cp) < one ? sqrt(cp) : one) : T(0);
+  st->ang_u = (double)(kind_row ? aq : ap);
+  st->ang_v = (double)(kind_row ? ap : aq);
+  if (st->kcap_nov > 0 && st->novelty > st->eta_nov) st->k = min(kt + 1, st->kcap_nov);
+}
+template <typename T>
+__device__ inline void append_signals(DevState* st, bool kind_row, const T* QK, const T* PK, int64_t ld, int r,
+                                      int k_out, bool grew, int kt) {
+  T cq = T(0), cp = T(0);
+  if (k_out <= r) {
+    for (int j = 0; j < k_out; ++j) {
+      const T a = QK[(int64_t)r * ld + j];
+      cq += a * a;
+      if (grew) {
+        const T b = PK[(int64_t)r * ld + j];
+        cp += b * b;
+      }
+    }
+  }
+  append_signals_sums<T>(st, kind_row, cq, cp, grew, kt);
+}
 
 // Optional phase timing (compile with -DISVD_CORE_TIMING): thread 0 of each CTA stores its
 // clock64() stamp i into isvd_core_clock[i] and adds it to isvd_core_clock_sum[i], so that for

@@ -34,14 +34,17 @@ cudaError_t pool_retry_set_attr();
 
 // Pool warp-per-update kernels k_pool_warp<kb> and row-parallel rotations k_pool_rotate<kb>
 // (kb = 8/16/32); scratch is the bucket run's first RotScratch<kb> record.
+// nblocks: entries of the run's block table; kcheck: the pool's self-check word (code, detail).
 cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
-                             void* scratch, const int* chunks, int* block_op, int rot_rows);
+                             void* scratch, const int* chunks, int* block_op, int rot_rows, int nblocks, int* kcheck);
 // Rows of one side per rotation block for rank bucket kb (the warp kernel's block tables).
 int pool_rot_rows(int kb, bool use_tc);
-// use_tc selects the tensor-core rotation (k_pool_rotate_tc, buckets 16 and 32), which loads its row
-// tiles through the pool's tensor maps (two per stream slot: U, V).
+// Both rotations load their row tiles through the pool's tensor maps (two per stream slot: U, V;
+// nmaps entries); use_tc selects the tensor-core one (k_pool_rotate_tc, buckets 16 and 32). nops:
+// the run's updates; kcheck: the pool's self-check word.
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
-                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps);
+                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps, int nops,
+                               int nmaps, int* kcheck);
 cudaError_t pool_warp_set_attrs();
 
 // Batched loss-of-orthogonality monitor / re-orthogonalisation (k_pool_reorth), one CTA per

@@ -30,6 +30,8 @@ struct PoolOp {
   int32_t sid;         // pool stream id (completion records)
   int32_t pad;
   int64_t seq;         // pool-wide sequence number of the op (completion records)
+  float* z1;           // per projection-side row: x - P p1 after the first projection pass (written by
+                       // the warp kernel of an append, read by its rotation for z_hat)
 };
 
 // A stream whose adaptive-rank check is due (Eq. evr-rank-rule read as a growth rule).
@@ -49,7 +51,6 @@ struct PoolCompletion {
 };
 
 
-constexpr int kPoolZMax = 4096;  // longest projection side handled by the fused kernel
 
 __host__ __device__ constexpr int pool_threads(int kb) {
   return kb <= 8 ? 128 : kb <= 16 ? 256 : kb <= 32 ? 288 : 544;
@@ -66,10 +67,9 @@ __host__ __device__ inline size_t pool_smem_bytes() {
   const size_t jac = core_smem_bytes<float>(KB);
   if (jac > core) core = jac;
   const size_t outs = (size_t)2 * (KB + 1) * KB * sizeof(float);          // U_K, V_K
-  const size_t zbuf = (size_t)kPoolZMax * sizeof(float);                    // z1 rows
   const size_t red = (size_t)(pool_threads(KB) / 32) * (KB + 4) * sizeof(double);
   const size_t vecs = (size_t)6 * (KB + 2) * sizeof(double);               // p1, p2, a, b, ...
-  return core + outs + zbuf + red + vecs + 256;
+  return core + outs + red + vecs + 256;
 }
 
 // Sum over the CTA's warps of per-warp column partials red[w][c] -> out[c] (FP64), c < cols.
@@ -228,8 +228,9 @@ __device__ void pool_tick_body(const PoolOp& op) {
   unsigned char* core_smem = smem;
   float* UKs = reinterpret_cast<float*>(smem + core_b);
   float* VKs = UKs + (KB + 1) * KB;
-  float* zbuf = VKs + (KB + 1) * KB;
-  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(zbuf + kPoolZMax) + 15) & ~uintptr_t(15));
+  // z1 rows of an append's projection side: the op's residual buffer in global memory (any length)
+  float* zbuf = op.z1;
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(VKs + (KB + 1) * KB) + 15) & ~uintptr_t(15));
   double* p1 = red + (size_t)nw * (KB + 4);
   double* p2 = p1 + (KB + 2);
   double* av = p2 + (KB + 2);
@@ -254,7 +255,7 @@ __device__ void pool_tick_body(const PoolOp& op) {
     // Pass 1: p1 = X^T x, ||x||^2.
     pool_project<KB>(Xp, op.ld, prow, op.x, r, red, p1, &s_sc[0]);
     ISVD_STAMP(17);
-    // Pass 2: z1 = x - X p1 per row (float-float, one thread per row) into zbuf, ||z1||^2.
+    // Pass 2: z1 = x - X p1 per row (float-float, one thread per row) into op.z1, ||z1||^2.
     float* p1h = reinterpret_cast<float*>(red);  // p1 as float pairs (red is free now)
     float* p1l = p1h + (KB + 2);
     for (int c = t; c < r; c += blockDim.x) {
@@ -387,6 +388,8 @@ __device__ void pool_tick_body(const PoolOp& op) {
     st->r = k_out;
     st->sweeps = s_sweeps;
     if (s_sweeps < 0) atomicOr(&st->status, kStNotConv);
+    if (kind == kEntry) st->ang_u = st->ang_v = 0.0;
+    else append_signals<float>(st, kind == kRow, UKs, VKs, KB, r, k_out, grew, in.kt);
   }
 }
 

@@ -31,8 +31,9 @@
 //   2. if the update or side changed: the core factor (V_K or U_K; rows >= r and columns >= k_out
 //      zeroed) is cut into digit planes (B operands, K-major) with per-column scales, four threads
 //      per column;
-//   3. each thread takes one row: z_hat = (x_row - row . p) / rho in float-float when the projection
-//      side gains the new direction, then the row's scale and digit planes (A operands);
+//   3. each thread takes one row: z_hat = (z1_row - row . p2) / rho when the projection side gains
+//      the new direction (z1 = x - P p1, the warp kernel's first-pass residual, computed there in
+//      float-float; p2 its small second-pass correction), then the row's scale and digit planes;
 //   4. thread 0 issues the six digit-product MMAs per K step of 16 (M = 128, N = KB, BF16, FP32
 //      accumulation) into the three level accumulators (TMEM, allocated once per CTA) and commits
 //      them to an mbarrier;
@@ -131,9 +132,8 @@ __global__ void __launch_bounds__(kTcRotThreads)
   unsigned char* Ad = smem + L::kOffA;
   unsigned char* Bd = smem + L::kOffB;
   float* zrow = reinterpret_cast<float*>(smem + L::kOffVec);
-  float* ph = zrow + KB;
-  float* pl = ph + KB;
-  float* bscale = pl + KB;
+  float* p2 = zrow + KB;  // the second-pass projection p2 (z_hat = (z1 - row . p2) / rho)
+  float* bscale = p2 + 2 * KB;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kOffBar);  // tile landed in stage 0 / 1
   uint64_t* mmab = full + 2;                                          // MMAs of a block completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmem);
@@ -215,8 +215,7 @@ __global__ void __launch_bounds__(kTcRotThreads)
       }
       if (tid < KB) {
         zrow[tid] = (blk.pside && tid < k_out) ? src[r * KB + tid] : 0.f;
-        ph[tid] = tid < r ? sc.ph[tid] : 0.f;
-        pl[tid] = tid < r ? sc.pl[tid] : 0.f;
+        p2[tid] = tid < r ? sc.p2[tid] : 0.f;
       }
       prev_e = blk.e;
       prev_side = blk.pside;
@@ -257,16 +256,10 @@ __global__ void __launch_bounds__(kTcRotThreads)
     }
     float zh = 0.f;
     if (blk.withz && live) {
-      ff sacc{op.x[blk.base + row], 0.f};
+      float corr = 0.f;  // the row's entries beyond r are zero
 #pragma unroll
-      for (int c = 0; c < KB; ++c) {
-        if (c < r) {
-          ff pr = two_prod(xv[c], ph[c]);
-          pr.lo = fmaf(xv[c], pl[c], pr.lo);
-          sacc = ff_add(sacc, ff{-pr.hi, -pr.lo});
-        }
-      }
-      zh = (sacc.hi + sacc.lo) * sc.inv_rho;
+      for (int c = 0; c < KB; ++c) corr = fmaf(xv[c], p2[c], corr);
+      zh = (op.z1[blk.base + row] - corr) * sc.inv_rho;
     }
     const int ea = fixed_exponent(amax);
     const float ascale = __int_as_float((127 + ea - 8) << 23);

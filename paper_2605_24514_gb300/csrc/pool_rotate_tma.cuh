@@ -7,14 +7,16 @@
 //     blocks (256 rows of one side of one update; the warp kernel's block -> update tables);
 //   - a producer warp per CTA brings every block's rows by TMA through the stream's tensor map of
 //     U or V (32-row boxes, swizzled so that a thread reading its own row meets no bank
-//     conflicts), together with the update's core factor (V_K or U_K) and p by bulk copies, on one
+//     conflicts), together with the update's core factor (V_K or U_K) and p2 by bulk copies, on one
 //     mbarrier per stage; three stages keep the next two blocks in flight while one is rotated;
 //   - four rotating warps take two rows per thread, rotated in place in shared memory (every
 //     core-factor value read feeds both rows), then write the block back with coalesced 16-byte
 //     stores and free the stage.
 // The arithmetic per row is fixed: y_j = sum_c x_c R[c][j] over the row's r entries (FMAs in c
-// order), then + z_hat R[r][j], with z_hat = (x_row - row . p) / rho in float-float, so results
-// do not depend on the tiling. Waits are bounded in wall time; on a timeout the stream's status
+// order), then + z_hat R[r][j], with z_hat = (z1_row - row . p2) / rho: z1 = x - P p1 is the warp
+// kernel's first-pass residual (formed there in float-float, which carries the cancellation) and
+// p2 = P^T z1 its small second-pass correction, so z = x - P (p1 + p2) needs only FP32 here.
+// Results do not depend on the tiling. Waits are bounded in wall time; on a timeout the stream's status
 // gets kStTimeout and the CTA stops after its copies in flight have landed (bounded).
 #pragma once
 
@@ -71,10 +73,16 @@ struct RotBlock {
   }
 };
 
-// First block at or after b (below b1) whose update has work (k_out >= 0), or b1.
+// First block at or after b (below b1) whose update has work (k_out >= 0), or b1. A table entry
+// outside [0, nops) stops the scan (the caller's checks reject that block).
 template <int KB>
-__device__ __forceinline__ int rot_next_live(const RotScratch<KB>* scratch, const int* block_op, int b, int b1) {
-  while (b < b1 && scratch[block_op[b]].k_out < 0) ++b;
+__device__ __forceinline__ int rot_next_live(const RotScratch<KB>* scratch, const int* block_op, int b, int b1,
+                                             int nops = 0x7fffffff) {
+  while (b < b1) {
+    const int e = block_op[b];
+    if (e < 0 || e >= nops || scratch[e].k_out >= 0) break;
+    ++b;
+  }
   return b;
 }
 
@@ -92,8 +100,8 @@ struct RotTmaLayout {
   static constexpr int kStages = 3;
   static constexpr uint32_t kTile = kPoolRotRows * KB * 4;     // one stage of rows
   static constexpr uint32_t kFactor = (KB + 1) * KB * 4;       // V_K or U_K (row stride KB)
-  static constexpr uint32_t kPvec = 2 * KB * 4;                // p as float pairs (hi, lo)
-  static constexpr uint32_t kXvec = kPoolRotRows * 4;          // the payload entries of the rows
+  static constexpr uint32_t kPvec = KB * 4;                    // p2
+  static constexpr uint32_t kXvec = kPoolRotRows * 4;          // the rows' first-pass residuals z1
   static constexpr uint32_t kOffF = kStages * kTile;
   static constexpr uint32_t kOffP = kOffF + kStages * kFactor;
   static constexpr uint32_t kOffX = kOffP + kStages * kPvec;
@@ -194,8 +202,42 @@ __device__ __forceinline__ void rot_two_rows(float* T, int a, int b, const float
   }
 }
 
+// Self-check codes recorded in the pool's check word (first failure wins; the block is skipped).
+constexpr int kChkBlockOp = 1;   // block -> update entry outside the run's updates
+constexpr int kChkChunk = 2;     // block outside its update's blocks
+constexpr int kChkRows = 3;      // block rows outside (0, 256] or past the side's rows
+constexpr int kChkMap = 4;       // stream id outside the tensor-map table, or a zeroed map
+constexpr int kChkRank = 5;      // r or k_out of the update outside [0, KB]
+constexpr int kChkWarpTable = 6; // the warp kernel's block table write past the run's table
+
+__device__ __forceinline__ void kcheck_record(int* kcheck, int code, int detail) {
+  if (atomicCAS(&kcheck[0], 0, code) == 0) kcheck[1] = detail;
+}
+
+// Producer-side validation of block b before any of its loads is issued.
+template <int KB>
+__device__ __forceinline__ bool rot_block_ok(const RotBlock<KB, kPoolRotRows>& bk, const PoolOp* ops,
+                                             const RotScratch<KB>* scratch, const int* chunk_start, int b,
+                                             int nops, int nmaps, const RowTensorMap* maps, int* kcheck) {
+  if (bk.e < 0 || bk.e >= nops) return kcheck_record(kcheck, kChkBlockOp, b), false;
+  if (b < chunk_start[bk.e]) return kcheck_record(kcheck, kChkChunk, b), false;
+  const PoolOp& op = ops[bk.e];
+  const int64_t nrows = bk.pside ? (op.kind == kRow ? op.n : op.m) : (op.kind == kRow ? op.m : op.n);
+  if (bk.rows <= 0 || bk.rows > kPoolRotRows || bk.base + bk.rows > nrows) return kcheck_record(kcheck, kChkRows, b), false;
+  if (op.sid < 0 || 2 * op.sid + 1 >= nmaps) return kcheck_record(kcheck, kChkMap, b), false;
+  const RotScratch<KB>& sc = scratch[bk.e];
+  if (sc.r < 0 || sc.r > KB || sc.k_out > KB) return kcheck_record(kcheck, kChkRank, b), false;
+  const uint64_t* mw = reinterpret_cast<const uint64_t*>(bk.tmap(ops, maps));
+  uint64_t any = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) any |= mw[i];
+  if (!any) return kcheck_record(kcheck, kChkMap, b), false;
+  return true;
+}
+
 // nblocks rotation blocks of one rank bucket's updates (tables from the warp kernel, 256 rows per
-// block); persistent CTAs, block range [blockIdx.x * per, (blockIdx.x + 1) * per).
+// block); persistent CTAs, block range [blockIdx.x * per, (blockIdx.x + 1) * per). nops: the run's
+// updates; nmaps: entries of the tensor-map table; kcheck: the pool's self-check word.
 // Warp specialisation: warp 4 is the producer (for each live block of the range: wait until the
 // stage is free, describe the block in the stage's RotMeta, stage the payload entries of the
 // rows, issue the TMA and bulk loads); warps 0-3 rotate (wait for the stage, rotate two rows per
@@ -205,7 +247,7 @@ template <int KB>
 __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
     k_pool_rotate(const PoolOp* __restrict__ ops, const RotScratch<KB>* __restrict__ scratch,
                   const int* __restrict__ chunk_start, const int* __restrict__ block_op, int nblocks,
-                  const RowTensorMap* __restrict__ maps) {
+                  const RowTensorMap* __restrict__ maps, int nops, int nmaps, int* __restrict__ kcheck) {
   using L = RotTmaLayout<KB>;
   constexpr int S = L::kStages;
   constexpr int C4 = KB / 4;
@@ -218,10 +260,15 @@ __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
 
   const int per = (nblocks + (int)gridDim.x - 1) / (int)gridDim.x;
   const int b1 = min(nblocks, ((int)blockIdx.x + 1) * per);
-  const int b0 = rot_next_live<KB>(scratch, block_op, (int)blockIdx.x * per, b1);
+  const int b0 = rot_next_live<KB>(scratch, block_op, (int)blockIdx.x * per, b1, nops);
   if (b0 >= b1) return;  // uniform: nothing to rotate in this range
+  const int e0 = block_op[b0];
+  DevState* st0 = e0 >= 0 && e0 < nops ? ops[e0].st : nullptr;  // where a failure of this CTA is reported
   if ((uint32_t)(smem - smem_raw) + L::kUsed > tc::dynamic_smem_bytes()) {  // uniform
-    if (tid == 0) atomicOr(&ops[block_op[b0]].st->status, kStLayout);
+    if (tid == 0) {
+      if (st0) atomicOr(&st0->status, kStLayout);
+      else kcheck_record(kcheck, kChkBlockOp, b0);
+    }
     return;
   }
 
@@ -253,12 +300,24 @@ __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
         break;
       }
       RotBlock<KB, kPoolRotRows> bk;
+      bk.e = block_op[b];
+      if (bk.e < 0 || bk.e >= nops) {
+        if (lane == 0) kcheck_record(kcheck, kChkBlockOp, b);
+        b = rot_next_live<KB>(scratch, block_op, b + 1, b1, nops);
+        --it;  // the stage stays free for the next block
+        continue;
+      }
       bk.locate(ops, scratch, chunk_start, block_op, b);
+      if (!rot_block_ok<KB>(bk, ops, scratch, chunk_start, b, nops, nmaps, maps, kcheck)) {
+        b = rot_next_live<KB>(scratch, block_op, b + 1, b1, nops);
+        --it;
+        continue;
+      }
       const RotScratch<KB>& sc = scratch[bk.e];
       if (bk.withz) {
-        const float* x = ops[bk.e].x + bk.base;
-        float* xs = reinterpret_cast<float*>(smem + L::kOffX + (uint32_t)s * L::kXvec);
-        for (int i = lane; i < bk.rows; i += 32) xs[i] = x[i];
+        const float* z1 = ops[bk.e].z1 + bk.base;
+        float* zs = reinterpret_cast<float*>(smem + L::kOffX + (uint32_t)s * L::kXvec);
+        for (int i = lane; i < bk.rows; i += 32) zs[i] = z1[i];
       }
       __syncwarp();
       if (lane == 0) {
@@ -280,13 +339,13 @@ __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
         for (int q = 0; q < nbox; ++q)
           tc::tma_load_2d(dst + q * kRowBoxRows * KB, tm, 0, (int)bk.base + q * kRowBoxRows, &full[s]);
         tc::bulk_g2s(smem + L::kOffF + (uint32_t)s * L::kFactor, bk.pside ? sc.RP : sc.RQ, L::kFactor, &full[s]);
-        if (bk.withz) tc::bulk_g2s(smem + L::kOffP + (uint32_t)s * L::kPvec, sc.ph, L::kPvec, &full[s]);
+        if (bk.withz) tc::bulk_g2s(smem + L::kOffP + (uint32_t)s * L::kPvec, sc.p2, L::kPvec, &full[s]);
       }
       ++issued;
-      b = rot_next_live<KB>(scratch, block_op, b + 1, b1);
+      b = rot_next_live<KB>(scratch, block_op, b + 1, b1, nops);
     }
     if (failed && lane == 0) {
-      atomicOr(&ops[block_op[b0]].st->status, kStTimeout);
+      if (st0) atomicOr(&st0->status, kStTimeout);
       // the loads of stages not yet consumed land (bounded) before the CTA's shared memory goes away
       for (int j = max(0, issued - S); j < issued; ++j)
         tc::mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, kRotWaitNs);
@@ -299,7 +358,7 @@ __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
     const int s = it % S;
     const bool got = tc::mbar_wait_bounded(&full[s], (uint32_t)(it / S) & 1u, kRotWaitNs);
     if (tc::named_bar_or(1, kRotConsumers, !got)) {
-      if (tid == 0) atomicOr(&ops[block_op[b0]].st->status, kStTimeout);
+      if (tid == 0 && st0) atomicOr(&st0->status, kStTimeout);
       return;
     }
     const RotMeta M = meta[s];
@@ -315,23 +374,17 @@ __global__ void __launch_bounds__(kRotThreadsAll, RotTmaLayout<KB>::kMinBlocks)
       rot_load_row<KB>(T, u1, M.r, x1);
       float z0 = 0.f, z1 = 0.f;
       if (M.withz) {
-        const float* ph = reinterpret_cast<const float*>(smem + L::kOffP + (uint32_t)s * L::kPvec);
-        const float* pl = ph + KB;
-        const float* xs = reinterpret_cast<const float*>(smem + L::kOffX + (uint32_t)s * L::kXvec);
-        ff s0{xs[t0], 0.f}, s1{xs[u1], 0.f};
+        // the rows' entries beyond r are zero, and so is p2 beyond r
+        const float* p2 = reinterpret_cast<const float*>(smem + L::kOffP + (uint32_t)s * L::kPvec);
+        const float* zs = reinterpret_cast<const float*>(smem + L::kOffX + (uint32_t)s * L::kXvec);
+        float c0 = 0.f, c1 = 0.f;
 #pragma unroll
         for (int c = 0; c < KB; ++c) {
-          if (c < M.r) {
-            ff q = two_prod(x0[c], ph[c]);
-            q.lo = fmaf(x0[c], pl[c], q.lo);
-            s0 = ff_add(s0, ff{-q.hi, -q.lo});
-            q = two_prod(x1[c], ph[c]);
-            q.lo = fmaf(x1[c], pl[c], q.lo);
-            s1 = ff_add(s1, ff{-q.hi, -q.lo});
-          }
+          c0 = fmaf(x0[c], p2[c], c0);
+          c1 = fmaf(x1[c], p2[c], c1);
         }
-        z0 = (s0.hi + s0.lo) * M.inv_rho;
-        z1 = (s1.hi + s1.lo) * M.inv_rho;
+        z0 = (zs[t0] - c0) * M.inv_rho;
+        z1 = (zs[u1] - c1) * M.inv_rho;
       }
       rot_two_rows<KB>(T, t0, u1, x0, x1, M.r, R, M.k_out, z0, z1, M.withz != 0, has1);
     }

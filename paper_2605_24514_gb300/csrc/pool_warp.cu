@@ -12,10 +12,11 @@ namespace isvd {
 namespace {
 template <int KB>
 void warp_launch(int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n, void* scratch,
-                 const int* chunks, int* block_op, int rot_rows) {
+                 const int* chunks, int* block_op, int rot_rows, int nblocks, int* kcheck) {
   const int blocks = (count + kWarpsPerBlock - 1) / kWarpsPerBlock;
   k_pool_warp<KB><<<blocks, 32 * kWarpsPerBlock, warp_block_smem<KB>(), s>>>(
-      ops, count, base, retry, retry_n, reinterpret_cast<RotScratch<KB>*>(scratch), chunks, block_op, rot_rows);
+      ops, count, base, retry, retry_n, reinterpret_cast<RotScratch<KB>*>(scratch), chunks, block_op, rot_rows,
+      nblocks, kcheck);
 }
 int device_sms() {
   static int sms = 0;
@@ -29,7 +30,7 @@ int device_sms() {
 // Persistent CTAs over contiguous ranges of the rotation blocks: as many as fit on the SMs.
 template <int KB>
 void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
-                   const int* block_op, const void* tmaps) {
+                   const int* block_op, const void* tmaps, int nops, int nmaps, int* kcheck) {
   static int per_sm = 0;
   if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pool_rotate<KB>, kRotThreadsAll,
                                                                     RotTmaLayout<KB>::kBytes) != cudaSuccess ||
@@ -41,7 +42,7 @@ void rotate_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* s
   if (grid <= 0) return;
   k_pool_rotate<KB><<<grid, kRotThreadsAll, RotTmaLayout<KB>::kBytes, s>>>(
       ops, reinterpret_cast<const RotScratch<KB>*>(scratch), chunks, block_op, nblocks,
-      reinterpret_cast<const RowTensorMap*>(tmaps));
+      reinterpret_cast<const RowTensorMap*>(tmaps), nops, nmaps, kcheck);
 }
 template <int KB>
 void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch, const int* chunks,
@@ -56,11 +57,11 @@ void rotate_tc_launch(int nblocks, cudaStream_t s, const PoolOp* ops, const void
 }  // namespace
 
 cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* ops, int base, int* retry, int* retry_n,
-                             void* scratch, const int* chunks, int* block_op, int rot_rows) {
+                             void* scratch, const int* chunks, int* block_op, int rot_rows, int nblocks, int* kcheck) {
   switch (kb) {
-    case 8: warp_launch<8>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
-    case 16: warp_launch<16>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
-    default: warp_launch<32>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows); break;
+    case 8: warp_launch<8>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows, nblocks, kcheck); break;
+    case 16: warp_launch<16>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows, nblocks, kcheck); break;
+    default: warp_launch<32>(count, s, ops, base, retry, retry_n, scratch, chunks, block_op, rot_rows, nblocks, kcheck); break;
   }
   return cudaGetLastError();
 }
@@ -68,16 +69,17 @@ cudaError_t pool_warp_launch(int kb, int count, cudaStream_t s, const PoolOp* op
 int pool_rot_rows(int kb, bool use_tc) { return use_tc && (kb == 16 || kb == 32) ? kTcRotRows : kPoolRotRows; }
 
 cudaError_t pool_rotate_launch(int kb, int nblocks, cudaStream_t s, const PoolOp* ops, const void* scratch,
-                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps) {
+                               const int* chunks, const int* block_op, bool use_tc, const void* tmaps, int nops,
+                               int nmaps, int* kcheck) {
   switch (kb) {
-    case 8: rotate_launch<8>(nblocks, s, ops, scratch, chunks, block_op, tmaps); break;
+    case 8: rotate_launch<8>(nblocks, s, ops, scratch, chunks, block_op, tmaps, nops, nmaps, kcheck); break;
     case 16:
       if (use_tc) rotate_tc_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
-      else rotate_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
+      else rotate_launch<16>(nblocks, s, ops, scratch, chunks, block_op, tmaps, nops, nmaps, kcheck);
       break;
     default:
       if (use_tc) rotate_tc_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
-      else rotate_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps);
+      else rotate_launch<32>(nblocks, s, ops, scratch, chunks, block_op, tmaps, nops, nmaps, kcheck);
       break;
   }
   return cudaGetLastError();

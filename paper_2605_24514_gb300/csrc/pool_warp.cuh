@@ -65,7 +65,7 @@ template <int KB>
 struct alignas(16) RotScratch {
   float RP[(KB + 1) * KB];  // V_K (row stride KB), row r = z_hat's when the rank grew
   float RQ[(KB + 1) * KB];  // U_K (row stride KB)
-  float ph[KB], pl[KB];     // p as float pairs
+  float p2[KB];             // p2 = P^T z1, the second projection pass (z = z1 - P p2)
   float inv_rho;
   int r, k_out, grew;       // k_out < 0: the update was handed to the CTA kernel
 };
@@ -117,98 +117,83 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   if (r < 1 || r > KB || ld != KB) return false;
   ISVD_WSTAMP_INIT(tp);
 
-  // The projection side as one contiguous float4 array (row stride ld == KB): lane L reads chunk
-  // (L mod CPL) of row (L div CPL) + (32 / CPL) i, so every load is coalesced and four are in flight;
-  // columns >= r are masked (stale values beyond the working rank).
-  constexpr int CPL = KB / 4;    // float4 chunks per row
-  constexpr int U4 = 4;          // loads in flight per lane
-  const int cq = lane % CPL;
+  // The projection side row by row, one row per lane (rows lane, lane + 32, ...): a lane loads its
+  // whole row (KB / 4 float4s; the next row's loads are issued before the current row is used), so
+  // every row-wise quantity (the residual z1 in float-float) stays inside the lane, and column sums
+  // over rows are per-lane accumulators reduced once at the end (a register transpose). Columns >= r
+  // are zeroed (stale values beyond the working rank).
+  constexpr int C4 = KB / 4;
   const float4* P4 = reinterpret_cast<const float4*>(P);
-  const int64_t nF = nP * CPL;
-  float msk[4];
+  auto load_row = [&](int64_t row, float (&v)[KB], float& xv) {
+    const bool ok = row < nP;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) msk[j] = 4 * cq + j < r ? 1.f : 0.f;
+    for (int q = 0; q < C4; ++q) {
+      const float4 a = ok ? P4[row * C4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[4 * q] = 4 * q < r ? a.x : 0.f;
+      v[4 * q + 1] = 4 * q + 1 < r ? a.y : 0.f;
+      v[4 * q + 2] = 4 * q + 2 < r ? a.z : 0.f;
+      v[4 * q + 3] = 4 * q + 3 < r ? a.w : 0.f;
+    }
+    xv = ok ? x[row] : 0.f;
+  };
 
   // Pass 1: p1 = P^T x and ||x||^2.
-  float a4[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
   ff xx{0.f, 0.f};
-  for (int64_t fb = 0; fb < nF; fb += 32 * U4) {  // warp-uniform trip count
-    float4 v[U4];
-    float xv[U4];
+  {
+    float vn[KB], xn;
+    load_row(lane, vn, xn);
+    for (int64_t row0 = 0; row0 < nP; row0 += 32) {  // warp-uniform trip count
+      float v[KB];
 #pragma unroll
-    for (int u = 0; u < U4; ++u) {
-      const int64_t f = fb + lane + 32 * u;
-      const bool ok = f < nF;
-      v[u] = ok ? P4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
-      xv[u] = ok ? x[f / CPL] : 0.f;
-    }
+      for (int c = 0; c < KB; ++c) v[c] = vn[c];
+      const float xv = xn;
+      if (row0 + 32 < nP) load_row(row0 + 32 + lane, vn, xn);
 #pragma unroll
-    for (int u = 0; u < U4; ++u) {
-      a4[0] = fmaf(v[u].x * msk[0], xv[u], a4[0]);
-      a4[1] = fmaf(v[u].y * msk[1], xv[u], a4[1]);
-      a4[2] = fmaf(v[u].z * msk[2], xv[u], a4[2]);
-      a4[3] = fmaf(v[u].w * msk[3], xv[u], a4[3]);
-      if (cq == 0) xx = ff_add(xx, two_prod(xv[u], xv[u]));
+      for (int c = 0; c < KB; ++c) acc[c] = fmaf(v[c], xv, acc[c]);
+      xx = ff_add(xx, two_prod(xv, xv));
     }
   }
-#pragma unroll
-  for (int o = CPL; o < 32; o <<= 1)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a4[j] += __shfl_xor_sync(kFull, a4[j], o);
+  const float p1v = warp_transpose_sum<KB>(acc, lane);  // column lane % KB
   xx = ff_group_sum<32>(xx);
-  if (lane < CPL)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) S.ph[4 * lane + j] = msk[j] * a4[j];
+  if (lane < KB) S.ph[lane] = lane < r ? p1v : 0.f;
   __syncwarp();
   ISVD_WSTAMP(17, tp);
 
-  // Pass 2 (CGS2): z1 = x - P p1 per row (float-float, the row's CPL lanes combine their chunks),
-  // p2 = P^T z1, ||z1||^2.
-  float p1c[4];
+  // Pass 2 (CGS2): z1 = x - P p1 per row (float-float, inside the row's lane), p2 = P^T z1, ||z1||^2.
+  // z1 is also kept for the rotation's z_hat (op.z1).
 #pragma unroll
-  for (int j = 0; j < 4; ++j) p1c[j] = S.ph[4 * cq + j];
-  float b4[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int c = 0; c < KB; ++c) acc[c] = 0.f;
   ff zz{0.f, 0.f};
-  for (int64_t fb = 0; fb < nF; fb += 32 * U4) {  // warp-uniform trip count
-    float4 v[U4];
-    float xv[U4];
+  {
+    float vn[KB], xn;
+    load_row(lane, vn, xn);
+    for (int64_t row0 = 0; row0 < nP; row0 += 32) {  // warp-uniform trip count
+      float v[KB];
 #pragma unroll
-    for (int u = 0; u < U4; ++u) {
-      const int64_t f = fb + lane + 32 * u;
-      const bool ok = f < nF;
-      v[u] = ok ? P4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
-      xv[u] = ok ? x[f / CPL] : 0.f;
-    }
+      for (int c = 0; c < KB; ++c) v[c] = vn[c];
+      const float xv = xn;
+      const int64_t row = row0 + lane;
+      if (row0 + 32 < nP) load_row(row0 + 32 + lane, vn, xn);
+      ff d0{0.f, 0.f}, d1{0.f, 0.f};  // two partial dot products (independent chains)
 #pragma unroll
-    for (int u = 0; u < U4; ++u) {
-      const float vv[4] = {v[u].x * msk[0], v[u].y * msk[1], v[u].z * msk[2], v[u].w * msk[3]};
-      ff d = two_prod(vv[0], p1c[0]);
-#pragma unroll
-      for (int j = 1; j < 4; ++j) d = ff_add(d, two_prod(vv[j], p1c[j]));
-      d = ff_group_sum<CPL>(d);
-      const ff zrow = ff_add(ff{xv[u], 0.f}, ff{-d.hi, -d.lo});
+      for (int c = 0; c < KB; c += 2) {
+        d0 = ff_add(d0, two_prod(v[c], S.ph[c]));
+        d1 = ff_add(d1, two_prod(v[c + 1], S.ph[c + 1]));
+      }
+      const ff d = ff_add(d0, d1);
+      const ff zrow = ff_add(ff{xv, 0.f}, ff{-d.hi, -d.lo});
       const float z1 = zrow.hi + zrow.lo;
+      if (row < nP) op.z1[row] = z1;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b4[j] = fmaf(vv[j], z1, b4[j]);
-      if (cq == 0) zz = ff_add(zz, ff_sqr(zrow));
+      for (int c = 0; c < KB; ++c) acc[c] = fmaf(v[c], z1, acc[c]);
+      zz = ff_add(zz, ff_sqr(zrow));
     }
   }
-#pragma unroll
-  for (int o = CPL; o < 32; o <<= 1)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b4[j] += __shfl_xor_sync(kFull, b4[j], o);
+  const float p2v = warp_transpose_sum<KB>(acc, lane);
   zz = ff_group_sum<32>(zz);
-  // p1 and p2 for column c = 4 lane + j on lanes < CPL; spread to one column per lane.
-  float p1v = 0.f, p2v = 0.f;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float t1 = __shfl_sync(kFull, a4[j], (lane >> 2) % CPL);
-    const float t2 = __shfl_sync(kFull, b4[j], (lane >> 2) % CPL);
-    if ((lane & 3) == j) {
-      p1v = t1;
-      p2v = t2;
-    }
-  }
   const float p1c_l = (lane < KB && lane < r) ? p1v : 0.f;  // p1[lane]
   const float p2c = (lane < KB && lane < r) ? p2v : 0.f;    // p2[lane]
   double pn = (double)p2c * (double)p2c;
@@ -452,10 +437,7 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     RS.RP[idx] = in ? S.RP[idx] : 0.f;
     RS.RQ[idx] = in ? S.RQ[idx] : 0.f;
   }
-  for (int c = lane; c < r; c += 32) {
-    RS.ph[c] = S.ph[c];
-    RS.pl[c] = S.pl[c];
-  }
+  if (lane < KB) RS.p2[lane] = p2c;  // zero beyond r
   if (lane == 0) {
     RS.inv_rho = grew ? (float)(1.0 / rho) : 0.f;
     RS.r = r;
@@ -468,6 +450,18 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     if (is_row) op.A[op.m * op.lda + c] = x[c];
     else op.A[c * op.lda + op.n] = x[c];
   }
+  // Successive-subspace angles: squared norms of the kept rows r of U_K and V_K (warp sums).
+  float cq = 0.f, cp = 0.f;
+  if (k_out <= r && lane < k_out) {
+    const float a = S.RQ[r * KB + lane], b = grew ? S.RP[r * KB + lane] : 0.f;
+    cq = a * a;
+    cp = b * b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cq += __shfl_xor_sync(kFull, cq, o);
+    cp += __shfl_xor_sync(kFull, cp, o);
+  }
   if (lane == 0) {
     st->rho = rho;
     st->grew = grew ? 1 : 0;
@@ -478,6 +472,7 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     st->k_out = k_out;
     st->r = k_out;
     st->sweeps = 102;
+    append_signals_sums<float>(st, is_row, cq, cp, grew, kt);
   }
   ISVD_WSTAMP(23, tp);
   return true;
@@ -486,14 +481,15 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
 // ops[0 .. count): row/column appends of streams in rank bucket KB, one warp each. Updates that
 // need the CTA kernel are listed in retry[] as base + index (count in *retry_n), untouched.
 // Also fills block_op[chunk_start[e] + i] = e for the update's rotation blocks (rot_rows rows of
-// one side per block: 256 for the FP32-pipe rotation, 128 for the tensor-core one).
+// one side per block: 256 for the FP32-pipe rotation, 128 for the tensor-core one), checking that
+// they fall inside the run's table of nblocks entries (else the pool's check word gets code 6).
 constexpr int kPoolRotThreads = 128;
 constexpr int kPoolRotRows = 2 * kPoolRotThreads;  // rows per rotation block (two per thread)
 template <int KB>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 8 ? 6 : KB <= 16 ? 5 : 3)
     k_pool_warp(const PoolOp* __restrict__ ops, int count, int base, int* __restrict__ retry,
                 int* __restrict__ retry_n, RotScratch<KB>* __restrict__ scratch, const int* __restrict__ chunk_start,
-                int* __restrict__ block_op, int rot_rows) {
+                int* __restrict__ block_op, int rot_rows, int nblocks, int* __restrict__ kcheck) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wid = threadIdx.x >> 5;
   const int e = blockIdx.x * kWarpsPerBlock + wid;
@@ -504,7 +500,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, KB <= 16 ? 6 : 5)
     const int64_t nP = op.kind == kRow ? op.n : op.m, nQ = op.kind == kRow ? op.m : op.n;
     const int nb = (int)((nP + rot_rows - 1) / rot_rows + (nQ + rot_rows - 1) / rot_rows);
     const int c0 = chunk_start[e];
-    for (int i = threadIdx.x & 31; i < nb; i += 32) block_op[c0 + i] = e;
+    if (c0 < 0 || c0 + nb > nblocks) {  // self-check: the host's table sizes disagree with the shapes
+      if ((threadIdx.x & 31) == 0 && atomicCAS(&kcheck[0], 0, 6) == 0) kcheck[1] = e;
+    } else {
+      for (int i = threadIdx.x & 31; i < nb; i += 32) block_op[c0 + i] = e;
+    }
   }
   const bool ok = warp_append<KB>(op, S, scratch[e]);
   if (!ok && (threadIdx.x & 31) == 0) {

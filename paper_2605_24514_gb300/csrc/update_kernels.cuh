@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
     st->r = k_out;
     st->sweeps = s_sweeps;
     if (s_sweeps < 0) atomicOr(&st->status, kStNotConv);
+    if (kind == kEntry) st->ang_u = st->ang_v = 0.0;
+    else append_signals<T>(st, kind == kRow, UK, VKo, ldo, r, k_out, in.grew != 0, in.kt);
   }
 }
 

@@ -48,6 +48,10 @@ def test_risk_and_covariance_errors_match_oracle(isvd, prec):
     dt = np.float64 if prec == 0 else np.float32
     tol_rel = 1e-10 if prec == 0 else 1e-5
     tol_abs = 1e-9 if prec == 0 else 5e-5
+    # The covariance error is evaluated through r x r Grams (||C1 - C2||^2 = ||C1||^2 + ||C2||^2 -
+    # 2 <C1, C2>), which cancels to about sqrt(eps) relative when the two covariances coincide (right
+    # after a refresh): that is the FP64 floor of this quantity, not of the factors.
+    tol_cov = 1e-7 if prec == 0 else 5e-5
     raw, fm = streams.make_panel(450, 60, 8, seed=17)
     raw = raw.astype(dt)
     R, _, _ = F.center_rows(raw.astype(np.float64), F.CAUSAL)
@@ -75,7 +79,7 @@ def test_risk_and_covariance_errors_match_oracle(isvd, prec):
                 assert abs(got["vol"] - vol) <= tol_rel * vol, day
                 assert abs(got["vol_opt"] - vol_opt) <= tol_rel * vol_opt, day
                 assert abs(got["risk_error"] - F.risk_error(o.V, o.s, Vopt, sopt, t, ww)) <= tol_abs, day
-                assert abs(got["cov_error"] - F.covariance_error(o.V, o.s, Vopt, sopt, t)) <= tol_abs, day
+                assert abs(got["cov_error"] - F.covariance_error(o.V, o.s, Vopt, sopt, t)) <= tol_cov, day
                 cov_norm = np.linalg.norm(F.lowrank_covariance(o.V, o.s, t))
                 assert abs(got["cov_norm"] - cov_norm) <= tol_rel * cov_norm, day
     cheap = g.risk(full=False)
