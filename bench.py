@@ -54,10 +54,10 @@ WORKLOADS = {
                                   "updates, FP64, periodic refresh 250, metrics every 50"),
 }
 HBM_PEAK_FALLBACK = 6800.0
-# DRAM bytes (read + write) of one launch from the ncu --set full capture summarised under
-# profiles/ (tick 1 of the default workload; later ticks differ by < 1%). Set to None whenever
-# the kernel changes until it is captured again.
-DRAM_TRAFFIC = {"k_pool_rotate<32>": None, "k_pool_rotate_tc<32>": None}
+# DRAM bytes (read + write) of one launch of the default workload (4,096 streams), from the one-pass
+# ncu capture of dram__bytes_read.sum and dram__bytes_write.sum summarised under profiles/ (tick 3;
+# ticks differ by about 1%). Set to None whenever the kernel changes until it is captured again.
+DRAM_TRAFFIC = {"k_pool_rotate<32>": 247250000, "k_pool_rotate_tc<32>": None}
 
 
 def measured_peaks():

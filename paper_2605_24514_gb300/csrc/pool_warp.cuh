@@ -279,7 +279,8 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   // in the offset u from the nearer pole. The lane's poles shifted to the origin live in RP
   // (column = lane) while it searches.
   float* sh = S.RP;
-  for (int j = lane; j < nc; j += 32) {
+  const int nc32 = nc < 32 ? nc : 32;  // roots 0..31 one per lane; root 32 (nc = 33) by the whole warp below
+  for (int j = lane; j < nc32; j += 32) {
     if (!((mask >> j) & 1ull)) {
       S.tau[j] = 0.f;
       S.org[j] = j;
@@ -339,6 +340,60 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     S.lhi[j] = lam.hi;
     S.llo[j] = lam.lo;
   }
+  if (nc > 32) {
+    // Root 32, the largest (above the last pole, nothing above it), by the whole warp: the same
+    // iteration as above with the secular sums split over the lanes (pole i on lane i, pole 32 on
+    // lane 0) and reduced by shuffles, so every lane runs the identical scalar update.
+    const int j = 32;
+    if (!((mask >> j) & 1ull)) {
+      if (lane == 0) {
+        S.tau[j] = 0.f;
+        S.org[j] = j;
+        S.lhi[j] = S.dhi[j];
+        S.llo[j] = S.dlo[j];
+      }
+    } else {
+      const ff lo{S.dhi[j], S.dlo[j]};
+      const float d_a = S.what[lane] > 0.f ? ff_sub_to_f(ff{S.dhi[lane], S.dlo[lane]}, lo) : 1e30f;
+      const float w_a = S.what[lane];
+      const float d_b = lane == 0 && S.what[32] > 0.f ? ff_sub_to_f(ff{S.dhi[32], S.dlo[32]}, lo) : 1e30f;
+      const float w_b = lane == 0 ? S.what[32] : 0.f;
+      float a = 0.f, b = ws, u = 0.5f * ws;
+      for (int it = 0; it < 40; ++it) {
+        float rq = __fdividef(1.f, d_a - u);
+        float t1 = w_a * rq;
+        float fs = t1, ds = t1 * rq;
+        rq = __fdividef(1.f, d_b - u);
+        t1 = w_b * rq;
+        fs += t1;
+        ds = fmaf(t1, rq, ds);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          fs += __shfl_xor_sync(kFull, fs, o);
+          ds += __shfl_xor_sync(kFull, ds, o);
+        }
+        fs = __shfl_sync(kFull, fs, 0);  // lane 0's sums everywhere: bit-identical control flow
+        ds = __shfl_sync(kFull, ds, 0);
+        const float h = 1.f + fs;
+        if (h == 0.f) break;
+        if (h < 0.f) a = u;
+        else b = u;
+        const float C = h + ds * u;
+        float un = (C > 0.f) ? ds * u * u / C : -1.f;
+        if (!(un > a && un < b)) un = (a > 0.f && b > 4.f * a) ? sqrtf(a) * sqrtf(b) : 0.5f * (a + b);
+        const bool done = fabsf(un - u) <= 1e-7f * un || (b - a) <= 2.4e-7f * b;
+        u = un;
+        if (done) break;
+      }
+      if (lane == 0) {
+        const ff lam = ff_add(lo, ff{u, 0.f});
+        S.tau[j] = u;
+        S.org[j] = j;
+        S.lhi[j] = lam.hi;
+        S.llo[j] = lam.lo;
+      }
+    }
+  }
   __syncwarp();
   ISVD_WSTAMP(20, tp);
 
@@ -346,7 +401,7 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   // root paired with its neighbouring pole; rejected when |w_hat - w| > kGeTolEps eps ||w||.
   const float tol = kGeTolEps * Eps<float>::v * sqrtf(wn2);
   int badge = 0;
-  for (int i = lane; i < nc; i += 32) {
+  for (int i = lane; i < nc32; i += 32) {
     float wh = 0.f;
     if ((mask >> i) & 1ull) {
       const ff di{S.dhi[i], S.dlo[i]};
@@ -368,6 +423,34 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
     }
     S.what[i] = wh;
   }
+  if (nc > 32) {
+    // w_hat_32 by the whole warp: factor j on lane j (and j = 32 on lane 0), a product butterfly.
+    const int i = 32;
+    const bool live = (mask >> i) & 1ull;
+    const ff di{S.dhi[i], S.dlo[i]};
+    auto factor = [&](int j) -> float {
+      if (!((mask >> j) & 1ull)) return 1.f;
+      const int o = S.org[j];
+      const float num = ff_sub_to_f(ff{S.dhi[o], S.dlo[o]}, di) + S.tau[j];
+      const int nj = warp_next_pole(mask, j);
+      if (nj < 0) return num;
+      const int pj = j < i ? j : nj;
+      return __fdividef(num, ff_sub_to_f(ff{S.dhi[pj], S.dlo[pj]}, di));
+    };
+    float prod = live ? factor(lane) * (lane == 0 ? factor(32) : 1.f) : 1.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(kFull, prod, o);
+    prod = __shfl_sync(kFull, prod, 0);
+    __syncwarp();
+    if (lane == 0) {
+      float wh = 0.f;
+      if (live) {
+        wh = copysignf(sqrtf(fmaxf(prod, 0.f)), S.w[i]);
+        if (!(fabsf(wh - S.w[i]) <= tol)) badge = 1;
+      }
+      S.what[i] = wh;
+    }
+  }
   if (__any_sync(kFull, badge)) {
     ISVD_WCOUNT(30);
     return false;
@@ -377,7 +460,7 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
   // filled exactly once; anything else (a NaN root) hands the update back.
   for (int j = lane; j < nc; j += 32) S.perm[j] = -1;
   __syncwarp();
-  for (int j = lane; j < nc; j += 32) {
+  for (int j = lane; j < nc32; j += 32) {
     const float hj = S.lhi[j], lj = S.llo[j];
     int rk = 0;
     for (int l = 0; l < nc; ++l) {
@@ -385,6 +468,15 @@ __device__ bool warp_append(const PoolOp& op, WarpSmem<KB>& S, RotScratch<KB>& R
       rk += (hl > hj) || (hl == hj && (ll > lj || (ll == lj && l < j)));
     }
     if (rk < nc) S.perm[rk] = j;
+  }
+  if (nc > 32) {
+    // rank of root 32 by the whole warp: lane l compares root l (root 32 never outranks itself)
+    const int j = 32;
+    const float hj = S.lhi[j], lj = S.llo[j];
+    const float hl = S.lhi[lane], ll = S.llo[lane];
+    const bool beats = (hl > hj) || (hl == hj && (ll > lj || (ll == lj && lane < j)));
+    const int rk = __popc(__ballot_sync(kFull, beats));
+    if (lane == 0 && rk < nc) S.perm[rk] = j;
   }
   __syncwarp();
   int unset = 0;
