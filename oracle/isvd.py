@@ -15,8 +15,8 @@ Every routine follows the paper's steps in its own order and notation:
 * principal angles ........................... Section 2.4, Eqs. (theta-max), (angle-metrics-ref/opt)
 * Frobenius errors, ratio, EVR, N_t .......... Section 2.5, Eqs. (frob-errors), (frob-ratio), (evr)
 * refresh and rank policies .................. Section 3, Eqs. (periodic-refresh-rule),
-                                               (error-refresh-rule), angle rule, (evr-rank-rule),
-                                               (novelty-rank-rule)
+                                               (error-refresh-rule), angle rule, (evr-rank-rule)
+                                               with its shrink side, (novelty-rank-rule)
 * successive-subspace angles ................. Section 3.3 ("subspace-change per update")
 
 Readings taken where the paper is silent or ambiguous are stated inline (marked
@@ -38,6 +38,7 @@ POLICY_ERROR = 2
 POLICY_ANGLE = 4
 POLICY_ADAPTIVE_RANK = 8
 POLICY_NOVELTY_RANK = 16
+POLICY_RANK_SHRINK = 32
 
 
 # ---------------------------------------------------------------------------
@@ -161,6 +162,7 @@ class Policy:
     gamma: float = 1.1
     theta_max: float = np.pi / 2
     tau_evr: float = 0.9
+    tau_shrink: float = 0.99
     k_min: int = 1
     k_max: int = 0
     store_initial_subspace: bool = False
@@ -407,8 +409,17 @@ class OracleISVD:
                 fire = True                               # angle-based rule, Section 3.3
             if pol.kind & POLICY_ADAPTIVE_RANK and np.isfinite(mt.evr) and mt.evr < pol.tau_evr:
                 # Reading of Eq. (evr-rank-rule) as "grow k while EVR < tau", one step
-                # per check, bounded by k_max; no shrink.
+                # per check, bounded by k_max.
                 self.k = min(self.k + 1, pol.k_max if pol.k_max > 0 else self.k + 1)
+            elif pol.kind & POLICY_RANK_SHRINK and self.k > max(pol.k_min, 1) and self.N > 0:
+                # The shrink side (Section 6's remark, and Eq. (evr-rank-rule)'s smallest k): when
+                # the leading k - 1 components alone explain at least tau_shrink of N_t (a target
+                # above tau, the hysteresis against oscillation), k <- k - 1 and the smallest
+                # maintained component is dropped, one step per check, bounded by k_min.
+                evr_km1 = float(np.sum(self.s[:self.k - 1] ** 2) / self.N)
+                if evr_km1 >= pol.tau_shrink:
+                    self.k -= 1
+                    self.U, self.s, self.V = truncate(self.U, self.s, self.V, self.k)
         if fire:
             self.refresh()
         if mt is not None:

@@ -112,3 +112,60 @@ def test_planted_reversed_novelty_comparison_fails_the_pin():
     o = Reversed(A0, 4, policy=oracle.Policy(kind=oracle.POLICY_NOVELTY_RANK, eta=0.3, k_max=8))
     o.append_row(o.V @ rng.standard_normal(o.r))
     assert o.k != 4
+
+
+def _three_factor_stream(k, **pol):
+    """A panel with three orthogonal components of energies 100, 25 and 4 (sigma 10, 5, 2) and
+    negligible noise: EVR(1) = 100 / 129, EVR(2) = 125 / 129, EVR(3) ~ 1."""
+    m, n = 50, 20
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, 3)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, 3)))
+    A0 = (Q1 * np.array([10.0, 5.0, 2.0])) @ Q2.T + 1e-6 * rng.standard_normal((m, n))
+    return oracle.OracleISVD(A0, k, tol_rel=1e-10, policy=oracle.Policy(**pol))
+
+
+def test_rank_shrink_stops_at_the_smallest_k_whose_k_minus_1_components_fall_short():
+    # shrink while EVR(k - 1) >= 0.99: from k = 6 down to 3, where EVR(2) = 125 / 129 < 0.99
+    o = _three_factor_stream(6, kind=oracle.POLICY_ADAPTIVE_RANK | oracle.POLICY_RANK_SHRINK,
+                             check_every=1, tau_evr=0.9, tau_shrink=0.99, k_min=1, k_max=8)
+    for t in range(6):
+        o.update_entry(t, t, 0.0)                      # a no-op update: one check per step
+    assert o.k == 3 and o.r == 3
+    np.testing.assert_allclose(o.s, [10.0, 5.0, 2.0], rtol=1e-6)
+    # with tau_shrink = 0.96, EVR(2) = 0.969 also qualifies: one more step down to 2
+    o2 = _three_factor_stream(6, kind=oracle.POLICY_ADAPTIVE_RANK | oracle.POLICY_RANK_SHRINK,
+                              check_every=1, tau_evr=0.5, tau_shrink=0.96, k_min=1, k_max=8)
+    for t in range(6):
+        o2.update_entry(t, t, 0.0)
+    assert o2.k == 2 and o2.r == 2
+
+
+def test_rank_shrink_respects_k_min_and_needs_the_flag():
+    o = _three_factor_stream(6, kind=oracle.POLICY_ADAPTIVE_RANK | oracle.POLICY_RANK_SHRINK,
+                             check_every=1, tau_evr=0.9, tau_shrink=0.99, k_min=5, k_max=8)
+    for t in range(4):
+        o.update_entry(t, t, 0.0)
+    assert o.k == 5
+    o = _three_factor_stream(6, kind=oracle.POLICY_ADAPTIVE_RANK, check_every=1, tau_evr=0.9)
+    for t in range(4):
+        o.update_entry(t, t, 0.0)
+    assert o.k == 6                                    # growth-only rule: EVR ~ 1 >= tau, no change
+
+
+def test_planted_shrink_on_evr_of_k_fails_the_pin():
+    """Comparing EVR(k) instead of EVR(k - 1) shrinks one step too far (to k = 2)."""
+    class Wrong(oracle.OracleISVD):
+        def _after_update(self):
+            self.t += 1
+            evr_k = float(np.sum(self.s[:self.k] ** 2) / self.N)
+            if self.k > 1 and evr_k >= self.policy.tau_shrink:
+                self.k -= 1
+                self.U, self.s, self.V = oracle.truncate(self.U, self.s, self.V, self.k)
+    m, n = 50, 20
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, 3)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, 3)))
+    A0 = (Q1 * np.array([10.0, 5.0, 2.0])) @ Q2.T + 1e-6 * rng.standard_normal((m, n))
+    o = Wrong(A0, 6, policy=oracle.Policy(kind=oracle.POLICY_RANK_SHRINK, tau_shrink=0.99))
+    for t in range(6):
+        o.update_entry(t, t, 0.0)
+    assert o.k != 3
