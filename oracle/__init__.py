@@ -6,5 +6,5 @@ may import this package. It shares no code with the CUDA path and never imports 
 from .isvd import (COL, ENTRY, POLICY_ADAPTIVE_RANK, POLICY_ANGLE, POLICY_ERROR, POLICY_NOVELTY_RANK,  # noqa: F401
                    POLICY_RANK_SHRINK,
                    POLICY_NONE, POLICY_PERIODIC, ROW, Metrics, OracleISVD, Policy,
-                   col_append_update, rank_one_update, row_append_update,
+                   col_append_update, rank_one_update, rank_one_update_exact, row_append_update,
                    theta_max, truncate, truncated_svd)

@@ -11,6 +11,7 @@ Every routine follows the paper's steps in its own order and notation:
 * row append ................................. Section 2.2, Eq. (row-residual), Algorithm A1
 * column append via transpose ................ Section 2.2 ("Column Append via Transpose"), Algorithm A2
 * rank-1 entry update (projection rule) ...... Section 2.3, Eq. (rank1-projection), Algorithm A3
+* rank-1 entry update, rank-increasing form ... Section 2.3's modification in Brand's general form
 * refresh / truncated SVD .................... Section 2.4 ("Refresh Operation")
 * principal angles ........................... Section 2.4, Eqs. (theta-max), (angle-metrics-ref/opt)
 * Frobenius errors, ratio, EVR, N_t .......... Section 2.5, Eqs. (frob-errors), (frob-ratio), (evr)
@@ -113,6 +114,45 @@ def rank_one_update(U, s, V, i, j, delta):
     K = np.diag(s) + delta * np.outer(su, sv)
     UK, sK, VKt = np.linalg.svd(K)
     return U @ UK, sK, V @ VKt.T
+
+
+def residual_direction(Q, e, tol_rel):
+    """Coordinates c = Q^T e of a unit vector e in span(Q) and its residual direction: e = Q c +
+    alpha d with d orthogonal to span(Q), alpha = ||e - Q c|| (two Gram-Schmidt passes, as for the
+    appends' residual); alpha <= tol_rel counts as zero (d = 0)."""
+    c = Q.T @ e
+    z = e - Q @ c
+    c2 = Q.T @ z
+    z = z - Q @ c2
+    c = c + c2
+    alpha = float(np.linalg.norm(z))
+    if alpha <= tol_rel:
+        return c, 0.0, np.zeros_like(e)
+    return c, alpha, z / alpha
+
+
+def rank_one_update_exact(U, s, V, i, j, delta, tol_rel):
+    """The rank-increasing form of the entry update (Brand's rank-one modification, the general
+    form of Section 2.3's A + delta e_i e_j^T that the projection rule, Eq. (rank1-projection),
+    approximates): with e_i = U p + alpha P and e_j = V q + beta Q,
+
+        U S V^T + delta e_i e_j^T = [U P] K [V Q]^T,  K = diag(S, 0) + delta [p; alpha] [q; beta]^T,
+
+    an (r+1) x (r+1) core; its SVD K = W S' Z^T gives U' = [U P] W and V' = [V Q] Z, exactly the
+    SVD of the updated low-rank matrix before truncation."""
+    m, n = U.shape[0], V.shape[0]
+    ei = np.zeros(m)
+    ei[i] = 1.0
+    ej = np.zeros(n)
+    ej[j] = 1.0
+    p, alpha, P = residual_direction(U, ei, tol_rel)
+    q, beta, Q = residual_direction(V, ej, tol_rel)
+    r = s.size
+    K = np.zeros((r + 1, r + 1))
+    K[:r, :r] = np.diag(s)
+    K += delta * np.outer(np.append(p, alpha), np.append(q, beta))
+    W, sK, Zt = np.linalg.svd(K)
+    return np.hstack([U, P[:, None]]) @ W, sK, np.hstack([V, Q[:, None]]) @ Zt.T
 
 
 def truncate(U, s, V, k):
@@ -309,6 +349,21 @@ class OracleISVD:
         self.N += 2.0 * delta * a_ij + delta * delta      # N_{t+1} = N_t + 2 delta A_ij + delta^2
         Av[i, j] = a_ij + delta                           # A_ij <- A_ij + delta
         U, s, V = rank_one_update(self.U, self.s, self.V, i, j, delta)
+        U0, V0 = self.U, self.V
+        self.U, self.s, self.V = truncate(U, s, V, self.k)
+        self._successive_angles(U0, V0)
+        self._after_update()
+
+    def update_entry_exact(self, i, j, delta):
+        """A_ij <- A_ij + delta through the rank-increasing core (rank_one_update_exact), then
+        truncation at k_t; the same bookkeeping and policy step as update_entry."""
+        i, j, delta = int(i), int(j), float(delta)
+        assert 0 <= i < self.m and 0 <= j < self.n
+        Av = self.A.view()
+        a_ij = float(Av[i, j])
+        self.N += 2.0 * delta * a_ij + delta * delta
+        Av[i, j] = a_ij + delta
+        U, s, V = rank_one_update_exact(self.U, self.s, self.V, i, j, delta, self.tol_rel)
         U0, V0 = self.U, self.V
         self.U, self.s, self.V = truncate(U, s, V, self.k)
         self._successive_angles(U0, V0)
