@@ -519,7 +519,7 @@ def run_batched(args):
         "dtype": "f32", "data": "synthetic (seeded factor-model panels and rows)",
         "config": {"workload": args.workload, "desc": W["desc"], "streams": S, "events_per_step": S,
                    "k_mix": {str(k): int(np.sum(ks == k)) for k in W["ks"]},
-                   "form": "per tick and rank bucket (8/16/32, concurrent streams): a warp-per-update projection + core launch and a row-parallel rotation launch; one hand-back launch",
+                   "form": "per rank bucket (8/16/32) on its own CUDA stream, so that the buckets' ticks overlap; per tick and bucket a warp-per-update projection + core launch, a persistent rotation launch, a hand-back launch and a completion-record launch",
                    "plain_form_updates_per_s": round(plain_value, 1) if plain_value else None,
                    "plain_form_ticks": plain_ticks, "plain_form_tick_ms_min_max": plain_spread,
                    "speedup_vs_plain": round(value / plain_value, 2) if plain_value else None,

@@ -83,6 +83,11 @@ typedef struct {
 #define ISVD_POLICY_NOVELTY_RANK 16  /* after a row or column append with rho > eta ||x||,
                                         k <- min(k + 1, k_max) for the next update, Eq.
                                         (novelty-rank-rule); decided on the device */
+#define ISVD_POLICY_RANK_SHRINK 32   /* at a check: if the leading k - 1 components explain at
+                                        least tau_shrink of N_t, k <- max(k - 1, k_min) and the
+                                        smallest component is dropped (the shrink side of Eq.
+                                        (evr-rank-rule), Section 6); tau_shrink above tau_evr
+                                        keeps the two rules from oscillating */
 
 typedef struct {
   int32_t kind;                    /* bit set of ISVD_POLICY_* */
@@ -95,6 +100,7 @@ typedef struct {
   double theta_max_rad;            /* angle threshold in radians */
   double tau_evr;                  /* EVR target */
   double eta;                      /* novelty threshold in (0, 1) (ISVD_POLICY_NOVELTY_RANK) */
+  double tau_shrink;               /* EVR of k - 1 components that shrinks k (ISVD_POLICY_RANK_SHRINK) */
 } isvd_policy;
 
 /* Metrics of Section 2.5 (names follow the paper). */
@@ -172,6 +178,15 @@ isvd_status isvd_append_col(isvd_t h, const void* y, int64_t m, int on_device);
  * U'S'V'^T = P_U (A_hat + delta e_i e_j^T) P_V at fixed rank, Eq. (rank1-projection). */
 isvd_status isvd_update_entry(isvd_t h, int64_t i, int64_t j, double delta);
 
+/* A_ij += delta in the rank-increasing form (Section 2.3's modification A + delta e_i e_j^T in
+ * Brand's general form, rather than its projection onto the current subspaces, Eq.
+ * rank1-projection): with e_i = U p + alpha P and e_j = V q + beta Q (p = U[i, :], q = V[j, :],
+ * alpha^2 = 1 - ||p||^2, beta^2 = 1 - ||q||^2; a residual norm <= tol_rel is dropped), the
+ * (r+1) x (r+1) core diag(sigma, 0) + delta [p; alpha][q; beta]^T is factorised and U' = [U P] U_K,
+ * V' = [V Q] V_K, truncated at k: the rank can grow by one. Same bookkeeping (A_ij, N_t, t) and
+ * policy step as isvd_update_entry; errors as there. */
+isvd_status isvd_update_entry_exact(isvd_t h, int64_t i, int64_t j, double delta);
+
 /* Applies nev events in order (same semantics as the three calls above, policy included).
  * payload holds the row/column vectors, host or device memory. */
 isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload,
@@ -240,9 +255,11 @@ const char* isvd_status_string(isvd_status s);
  * takes an ordered list of ops; ops of the same stream are applied in list order, ops of different
  * streams are grouped into "ticks" (at most one op per stream). Per tick, the appends of rank
  * buckets 8, 16 and 32 run as one launch per bucket of a warp-per-update kernel (projection with
- * CGS2, core SVD, dense-A and N_t bookkeeping) followed by one launch of a row-parallel rotation
- * kernel per bucket (tensor cores for buckets 16 and 32), the buckets on concurrent CUDA streams;
- * entry updates, bucket 64 and the updates the warp kernel hands back take a CTA-per-update kernel.
+ * CGS2, core SVD, dense-A and N_t bookkeeping) followed by one launch of a rotation kernel per
+ * bucket (FP32 pipes; tensor cores for buckets 16 and 32 with ISVD_POOL_TC_ROTATIONS); each bucket
+ * has its own internal CUDA stream, so ticks of different buckets overlap, and the pool's CUDA
+ * stream waits for them before its own work and at the end of every submit. Entry updates,
+ * bucket 64 and the updates the warp kernel hands back take a CTA-per-update kernel.
  * The launch count per tick does not depend on the number of streams. Streams are admitted under an
  * HBM budget; a staggered loss-of-orthogonality monitor re-orthonormalises streams as needed. The
  * pool path runs no refresh policy; isvd_pool_stream gives the stream's handle for refresh, metrics
@@ -271,6 +288,9 @@ typedef struct {
   double eta_novelty;        /* novelty rank rule for every stream (Eq. novelty-rank-rule): after an
                                 append with rho > eta_novelty ||x||, k <- min(k + 1, capacity) for
                                 the stream's next update; 0: off, else in (0, 1) */
+  double tau_shrink;         /* with rank_every: at the same checks, k <- k - 1 (at least 1) and the
+                                smallest component dropped when the leading k - 1 components
+                                explain at least tau_shrink of N_t; 0: off, else in (tau_evr, 1] */
 } isvd_pool_config;
 
 /* isvd_pool_config.flags */

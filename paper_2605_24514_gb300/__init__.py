@@ -20,6 +20,7 @@ FP64, FP32 = 0, 1
 ROW, COL, ENTRY = 0, 1, 2
 POLICY_NONE, POLICY_PERIODIC, POLICY_ERROR, POLICY_ANGLE, POLICY_ADAPTIVE_RANK = 0, 1, 2, 4, 8
 POLICY_NOVELTY_RANK = 16
+POLICY_RANK_SHRINK = 32
 METRICS_CHEAP, METRICS_FULL = 0, 1
 KCLASS = {"proj": 0, "core": 1, "rotate": 2, "check": 3, "refresh": 4, "reorth": 5}
 
@@ -45,7 +46,7 @@ class Policy(C.Structure):
     _fields_ = [("kind", C.c_int32), ("k_min", C.c_int32), ("k_max", C.c_int32),
                 ("store_initial_subspace", C.c_int32), ("T_refresh", C.c_int64), ("T_min", C.c_int64),
                 ("check_every", C.c_int64), ("gamma", C.c_double), ("theta_max_rad", C.c_double),
-                ("tau_evr", C.c_double), ("eta", C.c_double)]
+                ("tau_evr", C.c_double), ("eta", C.c_double), ("tau_shrink", C.c_double)]
 
 
 class Metrics(C.Structure):
@@ -66,7 +67,7 @@ class PoolConfig(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("flags", C.c_int32), ("max_streams", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("cuda_stream", C.c_void_p), ("tol_rel", C.c_double),
                 ("orth_every", C.c_int64), ("orth_tol", C.c_double), ("rank_every", C.c_int64),
-                ("tau_evr", C.c_double), ("eta_novelty", C.c_double)]
+                ("tau_evr", C.c_double), ("eta_novelty", C.c_double), ("tau_shrink", C.c_double)]
 
 
 POOL_TC_ROTATIONS = 1
@@ -115,6 +116,7 @@ _SIGS = {
     "isvd_append_row": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "isvd_append_col": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "isvd_update_entry": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double]),
+    "isvd_update_entry_exact": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double]),
     "isvd_apply_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int]),
     "isvd_set_policy": (C.c_int, [C.c_void_p, C.POINTER(Policy)]),
     "isvd_refresh": (C.c_int, [C.c_void_p, C.c_int]),
@@ -239,6 +241,10 @@ class ISVD:
     def update_entry(self, i, j, delta):
         self._check(lib().isvd_update_entry(self._h, int(i), int(j), float(delta)), "update_entry")
 
+    def update_entry_exact(self, i, j, delta):
+        """A_ij += delta in the rank-increasing form (both residual directions join the core)."""
+        self._check(lib().isvd_update_entry_exact(self._h, int(i), int(j), float(delta)), "update_entry_exact")
+
     def apply_events(self, events, payload=None):
         """Applies a ``streams.EventStream`` (payload converted to the storage type) in one call.
         ``payload`` may be given as a CUDA tensor to keep it on the device."""
@@ -258,10 +264,11 @@ class ISVD:
         self._check(lib().isvd_apply_events(self._h, arr, n, p, plen, d), "apply_events")
 
     def set_policy(self, kind=POLICY_NONE, T_refresh=0, T_min=0, check_every=0, gamma=1.1,
-                   theta_max=np.pi / 2, tau_evr=0.9, k_min=1, k_max=0, store_initial_subspace=False, eta=0.5):
+                   theta_max=np.pi / 2, tau_evr=0.9, k_min=1, k_max=0, store_initial_subspace=False, eta=0.5,
+                   tau_shrink=0.99):
         pol = Policy(kind=kind, k_min=k_min, k_max=k_max, store_initial_subspace=int(store_initial_subspace),
                      T_refresh=T_refresh, T_min=T_min, check_every=check_every, gamma=gamma,
-                     theta_max_rad=theta_max, tau_evr=tau_evr, eta=eta)
+                     theta_max_rad=theta_max, tau_evr=tau_evr, eta=eta, tau_shrink=tau_shrink)
         self._check(lib().isvd_set_policy(self._h, C.byref(pol)), "set_policy")
 
     def refresh(self, store_initial_subspace=False):
@@ -437,10 +444,10 @@ class Pool:
     """Many independent FP32 streams updated by fused per-tick launches (isvd_pool_*)."""
 
     def __init__(self, k_max=32, max_streams=0, hbm_budget_bytes=0, stream=None, tol_rel=0.0, flags=0,
-                 orth_every=0, orth_tol=0.0, rank_every=0, tau_evr=0.9, eta_novelty=0.0):
+                 orth_every=0, orth_tol=0.0, rank_every=0, tau_evr=0.9, eta_novelty=0.0, tau_shrink=0.0):
         cfg = PoolConfig(k_max=k_max, flags=flags, max_streams=max_streams, hbm_budget_bytes=hbm_budget_bytes,
                          cuda_stream=stream or 0, tol_rel=tol_rel, orth_every=orth_every, orth_tol=orth_tol,
-                         rank_every=rank_every, tau_evr=tau_evr, eta_novelty=eta_novelty)
+                         rank_every=rank_every, tau_evr=tau_evr, eta_novelty=eta_novelty, tau_shrink=tau_shrink)
         h = C.c_void_p()
         st = lib().isvd_pool_create(C.byref(cfg), C.byref(h))
         if st:

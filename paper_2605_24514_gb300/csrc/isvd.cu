@@ -56,6 +56,7 @@ struct isvd_ctx {
   int64_t m_ref = 0, uref_cap = 0;
   int r_ref = 0;
   double* p = nullptr;
+  double* px = nullptr;  // rank-increasing entry update: p, q (stride kKmaxLimit + 2), alpha, beta
   double* part = nullptr;
   void* UK = nullptr;
   void* VK = nullptr;
@@ -258,7 +259,7 @@ isvd_status launch_core(isvd_ctx* h, int kind, int64_t i, int64_t j, double delt
   const size_t cs = core_kernel_smem<T>(h->kmax);
   const int th = core_threads(h->kmax);
   CK(h, core_launch<T>(kb_bucket(h->kmax), th, cs, h->stream, kind, h->st, h->sig, h->p, (T*)h->U, (T*)h->V, h->ld, i,
-                       j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld));
+                       j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld, h->px, h->tol_rel));
   CKL(h);
   return ISVD_OK;
 }
@@ -484,6 +485,43 @@ isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
   sv.X = sv.Y = V;
   sv.rows = h->n;
   sv.R = h->VK;
+  prof_begin(h, ISVD_KCLASS_ROTATE, 2.0 * (h->m + h->n) * kk * h->es);
+  isvd_status s = launch_rotate<T>(h, su, sv, kb_bucket(h->kmax), (const T*)nullptr, h->p);
+  prof_end(h);
+  return s;
+}
+
+// Rank-1 entry update in the rank-increasing form: the core is diag(sigma, 0) + delta [p; alpha]
+// [q; beta]^T and each side gains its residual direction, P = (e_i - U p) / alpha and
+// Q = (e_j - V q) / beta, formed row by row in the rotations.
+template <typename T>
+isvd_status do_entry_exact(isvd_ctx* h, int64_t i, int64_t j, double delta) {
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  const double kk = (double)h->k_host;
+  prof_begin(h, ISVD_KCLASS_CORE, 2.0 * (kk + 1) * (kk + 1) * h->es);
+  isvd_status s0 = launch_core<T>(h, kEntryX, i, j, delta);
+  if (s0) return s0;
+  prof_end(h);
+  RotSide su{}, sv{};
+  su.X = su.Y = U;
+  su.rows = h->m;
+  su.ldx = su.ldy = h->ld;
+  su.ldr = h->ld;
+  su.c_in = -1;
+  su.k_out = -1;
+  su.R = h->UK;
+  su.zhat = 1;
+  su.zp = h->px;
+  su.zrho = h->px + 2 * (kKmaxLimit + 2);
+  su.zunit = i;
+  sv = su;
+  sv.X = sv.Y = V;
+  sv.rows = h->n;
+  sv.R = h->VK;
+  sv.zp = h->px + (kKmaxLimit + 2);
+  sv.zrho = h->px + 2 * (kKmaxLimit + 2) + 1;
+  sv.zunit = j;
   prof_begin(h, ISVD_KCLASS_ROTATE, 2.0 * (h->m + h->n) * kk * h->es);
   isvd_status s = launch_rotate<T>(h, su, sv, kb_bucket(h->kmax), (const T*)nullptr, h->p);
   prof_end(h);
@@ -1049,6 +1087,20 @@ isvd_status after_update(isvd_ctx* h) {
           CK(h, cudaMemcpyAsync(&h->st->k, &h->k_host, sizeof(int), cudaMemcpyHostToDevice, h->stream));
           CK(h, cudaStreamSynchronize(h->stream));
         }
+      } else if ((pol.kind & ISVD_POLICY_RANK_SHRINK) && h->k_host > std::max(pol.k_min, 1) && mt.N > 0.0) {
+        // The shrink side: the leading k - 1 maintained components against N_t.
+        const int keep = std::min(h->k_host - 1, (int)mt.r);
+        std::vector<double> sg(keep);
+        if (keep > 0) CK(h, cudaMemcpy(sg.data(), h->sig, 8 * (size_t)keep, cudaMemcpyDeviceToHost));
+        double ss = 0.0;
+        for (double v : sg) ss += v * v;
+        if (ss / mt.N >= pol.tau_shrink) {
+          h->k_host -= 1;
+          const int rnew = std::min((int)mt.r, h->k_host);
+          CK(h, cudaMemcpyAsync(&h->st->k, &h->k_host, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+          CK(h, cudaMemcpyAsync(&h->st->r, &rnew, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+          CK(h, cudaStreamSynchronize(h->stream));
+        }
       }
       h->last_check = mt;
     }
@@ -1097,6 +1149,7 @@ isvd_status create_impl(isvd_ctx* h, const void* A0, int64_t m0, int64_t n0, int
   if ((s = dmalloc(h, (void**)&h->st, sizeof(DevState)))) return s;
   if ((s = dmalloc(h, (void**)&h->sig, (kKmaxLimit + 2) * 8))) return s;
   if ((s = dmalloc(h, (void**)&h->p, (kKmaxLimit + 2) * 8))) return s;
+  if ((s = dmalloc(h, (void**)&h->px, (2 * (kKmaxLimit + 2) + 2) * 8))) return s;
   if ((s = dmalloc(h, (void**)&h->part, (size_t)kMaxProjBlocks * kPartStride * 8))) return s;
   if ((s = dmalloc(h, &h->UK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
   if ((s = dmalloc(h, &h->VK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
@@ -1270,6 +1323,16 @@ isvd_status isvd_update_entry(isvd_t h, int64_t i, int64_t j, double delta) {
   return h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h);
 }
 
+isvd_status isvd_update_entry_exact(isvd_t h, int64_t i, int64_t j, double delta) {
+  if (!h) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  if (i < 0 || i >= h->m || j < 0 || j >= h->n) return fail(h, ISVD_EBOUNDS, "entry index out of range");
+  if (!std::isfinite(delta)) return fail(h, ISVD_ENONFINITE, "non-finite delta");
+  isvd_status s = h->prec == ISVD_FP64 ? do_entry_exact<double>(h, i, j, delta) : do_entry_exact<float>(h, i, j, delta);
+  if (s) return s;
+  return h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h);
+}
+
 isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload, int64_t payload_len,
                               int payload_on_device) {
   if (!h || (nev > 0 && !ev)) return ISVD_EINVAL;
@@ -1316,8 +1379,10 @@ isvd_status isvd_set_policy(isvd_t h, const isvd_policy* pol) {
   }
   if (pol->T_refresh < 0 || pol->T_min < 0 || pol->check_every < 0) return ISVD_EINVAL;
   if (pol->kind & ~(ISVD_POLICY_PERIODIC | ISVD_POLICY_ERROR | ISVD_POLICY_ANGLE | ISVD_POLICY_ADAPTIVE_RANK |
-                    ISVD_POLICY_NOVELTY_RANK))
+                    ISVD_POLICY_NOVELTY_RANK | ISVD_POLICY_RANK_SHRINK))
     return fail(h, ISVD_EINVAL, "unknown policy kind bit");
+  if ((pol->kind & ISVD_POLICY_RANK_SHRINK) && !(pol->tau_shrink > 0.0 && pol->tau_shrink <= 1.0))
+    return fail(h, ISVD_EINVAL, "shrink threshold tau_shrink not in (0, 1]");
   if (pol->k_max > h->kmax) return fail(h, ISVD_EINVAL, "policy k_max exceeds the handle's k_max");
   const bool nov = (pol->kind & ISVD_POLICY_NOVELTY_RANK) != 0;
   if (nov && !(pol->eta > 0.0 && pol->eta < 1.0)) return fail(h, ISVD_EINVAL, "novelty threshold eta not in (0, 1)");
@@ -1513,6 +1578,7 @@ struct isvd_pool_ctx {
   int64_t rank_every = 0;
   double tau_evr = 0.9;
   double eta_nov = 0.0;  // novelty rank rule threshold (0: off)
+  double tau_shrink = 0.0;  // shrink side of the rank rule (0: off)
   std::vector<PoolRankOp> v_rank;
   std::vector<int64_t> v_rank_start;
   PoolRankOp* rank_dev = nullptr;
@@ -1556,7 +1622,7 @@ struct isvd_pool_ctx {
   int64_t block_op_cap = 0;
   // The rank buckets of a tick run concurrently on side streams (fork/join through events).
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_w[3] = {nullptr, nullptr, nullptr}, ev_r[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_r[3] = {nullptr, nullptr, nullptr};
   int num_sms = 152;
   // Per-stream scratch of a submit (valid where s_gen == gen), so that a submit touches only the
   // streams it names, and each stream's fused-kernel bucket (set at admission).
@@ -1624,14 +1690,13 @@ isvd_status pool_launch(isvd_pool_ctx* p, const PoolOp* ops, int count) {
   return ISVD_OK;
 }
 
-// One warp-per-update launch over ops[0 .. count) of rank bucket KB in tick t; hand-backs are
-// listed as base + index into the tick's warp ops.
+// One warp-per-update launch over ops[0 .. count) of rank bucket KB: scr is the run's rotation
+// scratch, hand-backs are listed in retry (as indexes into ops) and counted in *retry_n.
 template <int KB>
-isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, int base, int t,
-                             const int* chunks, int* block_op, int nblocks) {
-  void* scr = static_cast<char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
+isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, void* scr, int* retry,
+                             int* retry_n, const int* chunks, int* block_op, int nblocks) {
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_WARP8 : KB == 16 ? ISVD_POOL_KCLASS_WARP16 : ISVD_POOL_KCLASS_WARP32);
-  cudaError_t e = pool_warp_launch(KB, count, cs, ops, base, p->retry_list, p->retry_n + t, scr, chunks, block_op,
+  cudaError_t e = pool_warp_launch(KB, count, cs, ops, 0, retry, retry_n, scr, chunks, block_op,
                                    pool_rot_rows(KB, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0), nblocks, p->kcheck);
   pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool warp launch: ") + cudaGetErrorString(e));
@@ -1641,9 +1706,8 @@ isvd_status pool_launch_warp(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* op
 
 // Row-parallel rotations of a bucket run (chunks = its first-block table, nblocks in total).
 template <int KB>
-isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int base, const int* chunks,
+isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, const void* scr, const int* chunks,
                                const int* block_op, int nblocks, int count) {
-  const void* scr = static_cast<const char*>(p->rot_scratch) + (size_t)base * kRotScratchStride;
   pool_prof_begin(p, cs, KB == 8 ? ISVD_POOL_KCLASS_ROT8 : KB == 16 ? ISVD_POOL_KCLASS_ROT16 : ISVD_POOL_KCLASS_ROT32);
   cudaError_t e = pool_rotate_launch(KB, nblocks, cs, ops, scr, chunks, block_op, (p->flags & ISVD_POOL_TC_ROTATIONS) != 0,
                                      p->tmaps_dev, count, (int)(2 * p->tmaps_cap), p->kcheck);
@@ -1653,12 +1717,14 @@ isvd_status pool_launch_rotate(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* 
   return ISVD_OK;
 }
 
-// The CTA kernel over the updates the warps of tick t handed back (ops = the tick's warp ops).
-isvd_status pool_launch_retry(isvd_pool_ctx* p, const PoolOp* ops, int count, int t) {
+// The CTA kernel over the updates a warp launch handed back (ops = that launch's ops, retry and
+// retry_n its hand-back list and count), on the launch's stream.
+isvd_status pool_launch_retry(isvd_pool_ctx* p, cudaStream_t cs, const PoolOp* ops, int count, const int* retry,
+                              const int* retry_n) {
   const int rblocks = std::min(count, p->num_sms);
-  pool_prof_begin(p, p->stream, ISVD_POOL_KCLASS_RETRY);
-  cudaError_t e = pool_retry_launch(rblocks, p->stream, ops, p->retry_list, p->retry_n + t);
-  pool_prof_end(p, p->stream);
+  pool_prof_begin(p, cs, ISVD_POOL_KCLASS_RETRY);
+  cudaError_t e = pool_retry_launch(rblocks, cs, ops, retry, retry_n);
+  pool_prof_end(p, cs);
   if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool retry launch: ") + cudaGetErrorString(e));
   p->launches++;
   return ISVD_OK;
@@ -1782,6 +1848,7 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (cfg->k_max < 1 || cfg->k_max > kKmaxLimit) return ISVD_EINVAL;
   if (cfg->flags & ~(ISVD_POOL_TC_ROTATIONS | ISVD_POOL_COMPLETIONS | ISVD_POOL_DEVICE_CHECKS)) return ISVD_EINVAL;
   if (!(cfg->eta_novelty == 0.0 || (cfg->eta_novelty > 0.0 && cfg->eta_novelty < 1.0))) return ISVD_EINVAL;
+  if (!(cfg->tau_shrink == 0.0 || (cfg->tau_shrink > cfg->tau_evr && cfg->tau_shrink <= 1.0))) return ISVD_EINVAL;
   isvd_pool_ctx* p = new isvd_pool_ctx();
   p->kmax = cfg->k_max;
   p->kb = kb_bucket(cfg->k_max);
@@ -1795,6 +1862,7 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   p->rank_every = cfg->rank_every > 0 ? cfg->rank_every : 0;
   p->tau_evr = cfg->tau_evr;
   p->eta_nov = cfg->eta_novelty;
+  p->tau_shrink = cfg->tau_shrink;
   p->cfg.prec = ISVD_FP32;
   p->cfg.k_max = p->kmax;
   p->cfg.tol_rel = p->tol_rel;
@@ -1815,7 +1883,6 @@ isvd_status isvd_pool_create(const isvd_pool_config* cfg, isvd_pool_t* out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
     e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_w[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_r[i], cudaEventDisableTiming);
   }
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->stage[i].copied, cudaEventDisableTiming);
@@ -1846,7 +1913,6 @@ void isvd_pool_destroy(isvd_pool_t p) {
   if (p->block_op) cudaFree(p->block_op);
   for (int i = 0; i < 3; ++i) {
     if (p->side[i]) cudaStreamDestroy(p->side[i]);
-    if (p->ev_w[i]) cudaEventDestroy(p->ev_w[i]);
     if (p->ev_r[i]) cudaEventDestroy(p->ev_r[i]);
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -2156,21 +2222,21 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
   }
   int64_t tick_max = 0;
   for (int32_t t = 0; t < nticks; ++t) tick_max = std::max(tick_max, tick_start[t + 1] - tick_start[t]);
-  if (tick_max > p->retry_cap || nticks > p->retry_n_cap) {
+  if (tick_max > p->retry_cap || 3 * nticks > p->retry_n_cap) {
     cudaStreamSynchronize(p->stream);
     if (tick_max > p->retry_cap) {
       if (p->retry_list) cudaFree(p->retry_list);
       p->retry_list = nullptr;
       p->retry_cap = std::max<int64_t>(tick_max, 2 * p->retry_cap);
-      if (cudaMalloc((void**)&p->retry_list, sizeof(int) * (size_t)p->retry_cap) != cudaSuccess) {
+      if (cudaMalloc((void**)&p->retry_list, 3 * sizeof(int) * (size_t)p->retry_cap) != cudaSuccess) {
         p->retry_cap = 0;
         return pool_fail(p, ISVD_ENOMEM, "pool retry list");
       }
     }
-    if (nticks > p->retry_n_cap) {
+    if (3 * nticks > p->retry_n_cap) {
       if (p->retry_n) cudaFree(p->retry_n);
       p->retry_n = nullptr;
-      p->retry_n_cap = std::max<int64_t>(nticks, 2 * p->retry_n_cap);
+      p->retry_n_cap = std::max<int64_t>(3 * nticks, 2 * p->retry_n_cap);
       if (cudaMalloc((void**)&p->retry_n, sizeof(int) * (size_t)p->retry_n_cap) != cudaSuccess) {
         p->retry_n_cap = 0;
         return pool_fail(p, ISVD_ENOMEM, "pool retry counters");
@@ -2182,7 +2248,7 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
     if (p->rot_scratch) cudaFree(p->rot_scratch);
     p->rot_scratch = nullptr;
     p->rot_cap = std::max<int64_t>(tick_max, 2 * p->rot_cap);
-    if (cudaMalloc(&p->rot_scratch, kRotScratchStride * (size_t)p->rot_cap) != cudaSuccess) {
+    if (cudaMalloc(&p->rot_scratch, 3 * kRotScratchStride * (size_t)p->rot_cap) != cudaSuccess) {
       p->rot_cap = 0;
       return pool_fail(p, ISVD_ENOMEM, "pool rotation scratch");
     }
@@ -2393,8 +2459,35 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       return pool_fail(p, ISVD_ECUDA, "pool rank list copy");
   }
   cudaEventRecord(sg.copied, p->stream);
-  if (cudaMemsetAsync(p->retry_n, 0, sizeof(int) * (size_t)nticks, p->stream) != cudaSuccess)
+  if (cudaMemsetAsync(p->retry_n, 0, 3 * sizeof(int) * (size_t)nticks, p->stream) != cudaSuccess)
     return pool_fail(p, ISVD_ECUDA, "pool retry counters");
+  // Each rank bucket of the warp path has its own side stream and its own regions of the rotation
+  // scratch and hand-back lists, so consecutive ticks of one bucket are ordered by its stream and
+  // the buckets' ticks overlap. The main stream joins them only where it must: before work on the
+  // main stream (CTA-kernel and single-stream ops, the monitor, the rank rule), whose streams may
+  // have warp-path updates queued, and at the end of the submit; the side streams wait for the
+  // main stream again before their next work after it.
+  bool need_fork = true;
+  auto fork = [&]() -> isvd_status {
+    if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
+    for (int i = 0; i < 3; ++i)
+      if (cudaStreamWaitEvent(p->side[i], p->ev_fork, 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
+    need_fork = false;
+    return ISVD_OK;
+  };
+  bool side_busy = false;  // side streams hold work the main stream has not waited for
+  // Called before any work on the main stream: afterwards the side streams must wait for it.
+  auto join = [&]() -> isvd_status {
+    need_fork = true;
+    if (!side_busy) return ISVD_OK;
+    for (int i = 0; i < 3; ++i) {
+      if (cudaEventRecord(p->ev_r[i], p->side[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(p->stream, p->ev_r[i], 0) != cudaSuccess)
+        return pool_fail(p, ISVD_ECUDA, "pool join");
+    }
+    side_busy = false;
+    return ISVD_OK;
+  };
   for (int32_t t = 0; t < nticks; ++t) {
     // Fused ops of the tick are contiguous runs; ops outside the fused kernel's limits take the
     // single-stream kernels, in the same stream order.
@@ -2404,43 +2497,48 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
       int64_t q2 = q;
       while (q2 < tick_start[t + 1] && fused[q2] == fused[q] && (fused[q] != 1 || bucket_of(q2) == bucket_of(q))) ++q2;
       if (fused[q] == 2) {
-        // Per rank bucket (contiguous runs, widest first) on its own side stream: the warp
-        // launch, then its rotation launch. The hand-back launch runs on the main stream once all
-        // warp launches are done; the tick joins when all rotations are done.
-        if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
-        int nrun = 0;
-        for (int64_t b0 = q; b0 < q2; ++nrun) {
+        // Per rank bucket (contiguous runs, widest first) on the bucket's side stream: the warp
+        // launch, its rotation launch (which skips the updates handed back), the hand-back launch
+        // and (with completions) the records of the run's ops.
+        if (need_fork && (s = fork())) return s;
+        for (int64_t b0 = q; b0 < q2;) {
           int64_t b1 = b0;
           while (b1 < q2 && bucket_of(b1) == bucket_of(b0)) ++b1;
-          const int cnt = (int)(b1 - b0), base = (int)(b0 - q);
-          cudaStream_t cs = p->side[nrun];
+          const int cnt = (int)(b1 - b0);
+          const int bi = bucket_of(b0) == 8 ? 0 : bucket_of(b0) == 16 ? 1 : 2;
+          cudaStream_t cs = p->side[bi];
           int* bop = p->block_op + run_boff[b0];
           const int* ch = p->chunks_dev + b0;
-          if (cudaStreamWaitEvent(cs, p->ev_fork, 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool fork");
+          void* scr = static_cast<char*>(p->rot_scratch) + (size_t)bi * p->rot_cap * kRotScratchStride;
+          int* rlist = p->retry_list + (size_t)bi * p->retry_cap;
+          int* rcount = p->retry_n + 3 * t + bi;
+          const PoolOp* rops = p->ops_dev + b0;
           switch (bucket_of(b0)) {
-            case 8: s = pool_launch_warp<8>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
-            case 16: s = pool_launch_warp<16>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
-            default: s = pool_launch_warp<32>(p, cs, p->ops_dev + b0, cnt, base, t, ch, bop, run_blocks[b0]); break;
+            case 8: s = pool_launch_warp<8>(p, cs, rops, cnt, scr, rlist, rcount, ch, bop, run_blocks[b0]); break;
+            case 16: s = pool_launch_warp<16>(p, cs, rops, cnt, scr, rlist, rcount, ch, bop, run_blocks[b0]); break;
+            default: s = pool_launch_warp<32>(p, cs, rops, cnt, scr, rlist, rcount, ch, bop, run_blocks[b0]); break;
           }
           if (s) return s;
-          if (cudaEventRecord(p->ev_w[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
           switch (bucket_of(b0)) {
-            case 8: s = pool_launch_rotate<8>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
-            case 16: s = pool_launch_rotate<16>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
-            default: s = pool_launch_rotate<32>(p, cs, p->ops_dev + b0, base, ch, bop, run_blocks[b0], cnt); break;
+            case 8: s = pool_launch_rotate<8>(p, cs, rops, scr, ch, bop, run_blocks[b0], cnt); break;
+            case 16: s = pool_launch_rotate<16>(p, cs, rops, scr, ch, bop, run_blocks[b0], cnt); break;
+            default: s = pool_launch_rotate<32>(p, cs, rops, scr, ch, bop, run_blocks[b0], cnt); break;
           }
           if (s) return s;
-          if (cudaEventRecord(p->ev_r[nrun], cs) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
+          if ((s = pool_launch_retry(p, cs, rops, cnt, rlist, rcount))) return s;
+          if (completions) {
+            const cudaError_t e = pool_complete_launch(cnt, cs, rops, p->comp_dev + b0);
+            if (e != cudaSuccess)
+              return pool_fail(p, ISVD_ECUDA, std::string("pool completion launch: ") + cudaGetErrorString(e));
+            p->launches++;
+          }
+          side_busy = true;
           b0 = b1;
         }
-        for (int i = 0; i < nrun; ++i)
-          if (cudaStreamWaitEvent(p->stream, p->ev_w[i], 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
-        if ((s = pool_launch_retry(p, p->ops_dev + q, (int)(q2 - q), t))) return s;
-        for (int i = 0; i < nrun; ++i)
-          if (cudaStreamWaitEvent(p->stream, p->ev_r[i], 0) != cudaSuccess) return pool_fail(p, ISVD_ECUDA, "pool join");
         p->fused_ops += q2 - q;
         p->warp_ops += q2 - q;
       } else if (fused[q]) {
+        if ((s = join())) return s;
         const int cnt = (int)(q2 - q);
         switch (bucket_of(q)) {
           case 8: s = pool_launch<8>(p, p->ops_dev + q, cnt); break;
@@ -2450,7 +2548,14 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
         }
         if (s) return s;
         p->fused_ops += cnt;
+        if (completions) {
+          const cudaError_t e = pool_complete_launch(cnt, p->stream, p->ops_dev + q, p->comp_dev + q);
+          if (e != cudaSuccess)
+            return pool_fail(p, ISVD_ECUDA, std::string("pool completion launch: ") + cudaGetErrorString(e));
+          p->launches++;
+        }
       } else {
+        if ((s = join())) return s;
         for (int64_t z = q; z < q2; ++z) {
           const PoolOp& d = sg.ops[z];
           isvd_ctx* h = p->streams[ops[order[z]].stream];
@@ -2464,30 +2569,33 @@ isvd_status isvd_pool_submit(isvd_pool_t p, const isvd_op* ops, int64_t nops, co
           if (s) return s;
           p->fallback_ops++;
         }
+        if (completions) {
+          const cudaError_t e = pool_complete_launch((int)(q2 - q), p->stream, p->ops_dev + q, p->comp_dev + q);
+          if (e != cudaSuccess)
+            return pool_fail(p, ISVD_ECUDA, std::string("pool completion launch: ") + cudaGetErrorString(e));
+          p->launches++;
+        }
       }
       q = q2;
     }
     const int64_t nre = reorth_start[t + 1] - reorth_start[t];
+    const int64_t nrk = rank_start[t + 1] - rank_start[t];
+    if ((nre > 0 || nrk > 0) && (s = join())) return s;  // after this tick's updates of those streams
     if (nre > 0) {
       const cudaError_t e = pool_reorth_launch((int)nre, p->stream, p->reorth_dev + reorth_start[t], p->orth_tol);
       if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool monitor launch: ") + cudaGetErrorString(e));
       p->launches++;
       p->reorth_runs += nre;
     }
-    const int64_t nrk = rank_start[t + 1] - rank_start[t];
     if (nrk > 0) {
-      const cudaError_t e = pool_rank_launch((int)nrk, p->stream, p->rank_dev + rank_start[t], p->tau_evr);
+      const cudaError_t e =
+          pool_rank_launch((int)nrk, p->stream, p->rank_dev + rank_start[t], p->tau_evr, p->tau_shrink);
       if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool rank launch: ") + cudaGetErrorString(e));
-      p->launches++;
-    }
-    if (completions) {
-      const int64_t cnt = tick_start[t + 1] - tick_start[t];
-      const cudaError_t e = pool_complete_launch((int)cnt, p->stream, p->ops_dev + tick_start[t], p->comp_dev + tick_start[t]);
-      if (e != cudaSuccess) return pool_fail(p, ISVD_ECUDA, std::string("pool completion launch: ") + cudaGetErrorString(e));
       p->launches++;
     }
     p->ticks++;
   }
+  if ((s = join())) return s;  // the submit's work is complete when the main stream reaches here
   if (completions) {
     isvd_pool_ctx::CompBatch b;
     for (size_t i = 0; i < p->comp_free.size(); ++i)

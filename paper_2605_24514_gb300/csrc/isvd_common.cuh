@@ -21,6 +21,9 @@ constexpr int kStLayout = 8;  // a kernel's shared-memory layout did not fit its
 constexpr int kRow = 0;
 constexpr int kCol = 1;
 constexpr int kEntry = 2;
+// Entry update in the rank-increasing form (the core gains the two residual directions); core
+// kernels only, never a pool op kind.
+constexpr int kEntryX = 3;
 
 // Device-resident scalar state of one stream; read and written only by kernels, so a
 // sequence of updates needs no host round trip.

@@ -14,11 +14,12 @@ namespace isvd {
 
 struct PoolOp;
 
-// Core SVD kernel k_core<T, T, kb> (one CTA; kb = rank bucket 16/32/64/128).
+// Core SVD kernel k_core<T, T, kb> (one CTA; kb = rank bucket 16/32/64/128). px and tol_rel serve
+// the rank-increasing entry update (kind kEntryX).
 template <typename T>
 cudaError_t core_launch(int kb, int threads, size_t smem, cudaStream_t s, int kind, DevState* st, double* sig,
                         const double* p, const T* U, const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A,
-                        int64_t lda, T* UK, T* VKo, int ldo);
+                        int64_t lda, T* UK, T* VKo, int ldo, double* px, double tol_rel);
 // smem[b] = dynamic shared memory of bucket 16 << b (b = 0..3).
 template <typename T>
 cudaError_t core_set_attrs(const size_t smem[4]);
@@ -57,7 +58,7 @@ cudaError_t pool_reorth_launch(int count, cudaStream_t s, const PoolReorthOp* li
 struct PoolCompletion;
 struct PoolRankOp;
 // k <- min(k + 1, kcap) for every listed stream whose EVR = sum sigma^2 / N_t is below tau.
-cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau);
+cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau, double tau_shrink);
 cudaError_t pool_complete_launch(int count, cudaStream_t s, const PoolOp* ops, PoolCompletion* out);
 // out[s] = the status word of slot s's device state, s < n.
 cudaError_t pool_gather_status_launch(int64_t n, cudaStream_t s, const DevState* const* st, int* out);

@@ -123,22 +123,34 @@ __global__ void k_pool_gather_status(const DevState* const* __restrict__ st, int
   if (s < n) out[s] = st[s]->status;
 }
 // Adaptive rank (Eq. evr-rank-rule as a growth rule), one thread per listed stream.
-__global__ void k_pool_rank(const PoolRankOp* __restrict__ list, int count, double tau) {
+// The shrink side (tau_shrink > 0): when the leading k - 1 components explain at least tau_shrink
+// of N_t, k <- k - 1 (at least 1) and the maintained rank is cut to it.
+__global__ void k_pool_rank(const PoolRankOp* __restrict__ list, int count, double tau, double tau_shrink) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const PoolRankOp op = list[q];
   DevState* st = op.st;
-  const int r = st->r;
-  double ss = 0.0;
-  for (int c = 0; c < r; ++c) ss += op.sig[c] * op.sig[c];
+  const int r = st->r, k = st->k;
+  double ss = 0.0, ss_km1 = 0.0;
+  for (int c = 0; c < r; ++c) {
+    const double v = op.sig[c] * op.sig[c];
+    ss += v;
+    if (c < k - 1) ss_km1 += v;
+  }
   const double N = st->N;
-  if (N > 0.0 && ss / N < tau && st->k < op.kcap) st->k += 1;
+  if (!(N > 0.0)) return;
+  if (ss / N < tau) {
+    if (k < op.kcap) st->k = k + 1;
+  } else if (tau_shrink > 0.0 && k > 1 && ss_km1 / N >= tau_shrink) {
+    st->k = k - 1;
+    st->r = min(r, k - 1);
+  }
 }
 }  // namespace
 
-cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau) {
+cudaError_t pool_rank_launch(int count, cudaStream_t s, const PoolRankOp* list, double tau, double tau_shrink) {
   if (count <= 0) return cudaSuccess;
-  k_pool_rank<<<(count + 127) / 128, 128, 0, s>>>(list, count, tau);
+  k_pool_rank<<<(count + 127) / 128, 128, 0, s>>>(list, count, tau, tau_shrink);
   return cudaGetLastError();
 }
 

@@ -205,15 +205,21 @@ __global__ void __launch_bounds__(kProjThreads) k_proj2(const T* __restrict__ X,
 // every root), 512 for the 128 bucket (register budget).
 __host__ __device__ constexpr int core_max_threads(int kb) { return kb <= 64 ? 1024 : 512; }
 
+// kEntryX (the rank-increasing form): e_i = U p + alpha P, e_j = V q + beta Q with p = U[i, :],
+// q = V[j, :], alpha^2 = 1 - ||p||^2 and beta^2 = 1 - ||q||^2 (unit vectors against orthonormal
+// bases; a residual norm <= tol_rel counts as zero); the core is the (r+1) x (r+1) diagonal-plus-
+// rank-one matrix diag(sigma, 0) + delta [p; alpha] [q; beta]^T. px receives p, q (stride
+// kKmaxLimit + 2) and alpha, beta (at 2 (kKmaxLimit + 2) and + 1) for the rotations.
 template <typename T, typename JT, int KB>
 __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevState* st, double* sig, const double* __restrict__ p, const T* U,
                        const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A, int64_t lda, T* UK,
-                       T* VKo, int ldo) {
+                       T* VKo, int ldo, double* px, double tol_rel) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* ab = reinterpret_cast<double*>(smem);
   unsigned char* core_smem = smem + (size_t)2 * (kKmaxLimit + 1) * sizeof(double);
   const int r = st->r;
-  if (kind == kEntry) {
+  const bool entry = kind == kEntry || kind == kEntryX;
+  if (entry) {
     for (int c = threadIdx.x; c < r; c += blockDim.x) {
       ab[c] = (double)U[ei * (int64_t)ld + c];
       ab[kKmaxLimit + 1 + c] = (double)V[ej * (int64_t)ld + c];
@@ -226,10 +232,44 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
     }
   }
   __syncthreads();
+  bool grew_u = false, grew_v = false;
+  if (kind == kEntryX) {
+    // Residual norms of e_i and e_j (FP64 sums of the gathered rows), the extended core vectors.
+    __shared__ double s_ab[2];
+    if (threadIdx.x < 32) {
+      double su = 0.0, sv = 0.0;
+      for (int c = threadIdx.x; c < r; c += 32) {
+        su += ab[c] * ab[c];
+        sv += ab[kKmaxLimit + 1 + c] * ab[kKmaxLimit + 1 + c];
+      }
+      su = warp_sum(su);
+      sv = warp_sum(sv);
+      if (threadIdx.x == 0) {
+        const double al = sqrt(fmax(1.0 - su, 0.0)), be = sqrt(fmax(1.0 - sv, 0.0));
+        s_ab[0] = al > tol_rel ? al : 0.0;
+        s_ab[1] = be > tol_rel ? be : 0.0;
+      }
+    }
+    __syncthreads();
+    grew_u = s_ab[0] > 0.0;
+    grew_v = s_ab[1] > 0.0;
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+      px[c] = ab[c];
+      px[kKmaxLimit + 2 + c] = ab[kKmaxLimit + 1 + c];
+    }
+    if (threadIdx.x == 0) {
+      ab[r] = s_ab[0];
+      ab[kKmaxLimit + 1 + r] = s_ab[1];
+      px[2 * (kKmaxLimit + 2)] = s_ab[0];
+      px[2 * (kKmaxLimit + 2) + 1] = s_ab[1];
+      sig[r] = 0.0;  // the core's extra pole
+    }
+    __syncthreads();
+  }
   CoreIn in;
-  in.kind = kind;
-  in.r = r;
-  in.grew = (kind == kEntry) ? 0 : st->grew;
+  in.kind = entry ? kEntry : kind;
+  in.r = kind == kEntryX ? r + 1 : r;
+  in.grew = entry ? 0 : st->grew;
   in.kt = st->k;
   in.sig = sig;
   in.p = p;
@@ -239,7 +279,7 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
   in.delta = delta;
   __shared__ int s_sweeps;
   int k_out = -1;
-  if (sizeof(JT) < sizeof(double) && KB <= kFastCoreMaxKB) {
+  if (sizeof(JT) < sizeof(double) && KB <= kFastCoreMaxKB && kind != kEntryX) {
     // Secular-equation core (O(k^2) roots + verification); -1 means "use the Jacobi path".
     int it = 0;
     k_out = core_fast_cta<T, KB>(in, core_smem, UK, VKo, ldo, sig, &it);
@@ -254,8 +294,22 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
     st->r = k_out;
     st->sweeps = s_sweeps;
     if (s_sweeps < 0) atomicOr(&st->status, kStNotConv);
-    if (kind == kEntry) st->ang_u = st->ang_v = 0.0;
-    else append_signals<T>(st, kind == kRow, UK, VKo, ldo, r, k_out, in.grew != 0, in.kt);
+    if (kind == kEntry) {
+      st->ang_u = st->ang_v = 0.0;
+    } else if (kind == kEntryX) {
+      // both sides may have gained a direction: the angles from row r of U_K and of V_K
+      T cu = T(0), cv = T(0);
+      if (k_out <= r)
+        for (int j = 0; j < k_out; ++j) {
+          const T a = grew_u ? UK[(int64_t)r * ldo + j] : T(0), b = grew_v ? VKo[(int64_t)r * ldo + j] : T(0);
+          cu += a * a;
+          cv += b * b;
+        }
+      st->ang_u = (double)asin(sqrt(cu) < T(1) ? sqrt(cu) : T(1));
+      st->ang_v = (double)asin(sqrt(cv) < T(1) ? sqrt(cv) : T(1));
+    } else {
+      append_signals<T>(st, kind == kRow, UK, VKo, ldo, r, k_out, in.grew != 0, in.kt);
+    }
   }
 }
 
@@ -275,6 +329,12 @@ struct RotSide {
   int newrow;        // also write Y[rows, :] = R[c_in, :]
   int k_out;         // <0: take st->k_out
   const double* colscale;  // optional per-output-column scale (1 / sigma for U = A V S^-1)
+  // Residual direction of a unit vector e_zunit (rank-increasing entry update): when zrho is set,
+  // z_row = ([row == zunit] - X[row, :] . zp) / *zrho replaces the append's (xz[row] - X p) / rho,
+  // and the column is used only when *zrho > 0.
+  const double* zp;
+  const double* zrho;
+  int64_t zunit;
 };
 
 constexpr int kRotRows = 64;
@@ -299,7 +359,8 @@ __global__ void __launch_bounds__(kRotThreads) k_rotate(RotSide s0, RotSide s1, 
   const int c_in = sd.c_in >= 0 ? sd.c_in : st->r_in;
   const int k_out = sd.k_out >= 0 ? sd.k_out : st->k_out;
   if (c_in > KB || k_out > KB) return;  // the host picks KB >= both; never taken
-  const bool zhat = sd.zhat && st->grew;
+  const bool zhat = sd.zhat && (sd.zrho ? *sd.zrho > 0.0 : st->grew != 0);
+  const double* zp = sd.zrho ? sd.zp : p;
   const int nrr = c_in + (zhat || sd.newrow ? 1 : 0);
   const T* X = reinterpret_cast<const T*>(sd.X);
   T* Y = reinterpret_cast<T*>(sd.Y);
@@ -326,12 +387,13 @@ __global__ void __launch_bounds__(kRotThreads) k_rotate(RotSide s0, RotSide s1, 
   if (zhat) {
     const int rr = t >> 2, part = t & 3;
     double d = 0.0;
-    for (int c = part; c < c_in; c += 4) d += (double)Xs[c * (kRotRows + 1) + rr] * p[c];
+    for (int c = part; c < c_in; c += 4) d += (double)Xs[c * (kRotRows + 1) + rr] * zp[c];
     d += __shfl_xor_sync(0xffffffffu, d, 1);
     d += __shfl_xor_sync(0xffffffffu, d, 2);
     if (part == 0) {
       const int64_t row = row0 + rr;
-      zs[rr] = row < sd.rows ? (T)(((double)xz[row] - d) / st->rho) : T(0);
+      const double src = sd.zrho ? (row == sd.zunit ? 1.0 : 0.0) : (row < sd.rows ? (double)xz[row] : 0.0);
+      zs[rr] = row < sd.rows ? (T)((src - d) / (sd.zrho ? *sd.zrho : st->rho)) : T(0);
     }
     __syncthreads();
   }

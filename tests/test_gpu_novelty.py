@@ -1,6 +1,7 @@
-"""The novelty rank rule (Eq. novelty-rank-rule) and the successive-subspace angles (Section 3.3,
-"subspace-change per update") on the GPU against the oracle, through the C ABI: a single stream in
-both precisions (60/20/20 row/column/entry mix) and pool streams in the warp-per-update path.
+"""The novelty rank rule (Eq. novelty-rank-rule), the shrink side of the EVR rank rule (Eq.
+evr-rank-rule, Section 6) and the successive-subspace angles (Section 3.3, "subspace-change per
+update") on the GPU against the oracle, through the C ABI: a single stream in both precisions
+(60/20/20 row/column/entry mix) and pool streams.
 
 The rule is decided on the device after each append; the working rank k_t the library reports
 must follow the oracle's step by step. Inputs: a factor-model panel with 8 factors and low noise,
@@ -111,4 +112,85 @@ def test_pool_novelty_rule_and_successive_angles(isvd):
     for sidx, o in enumerate(orc):
         s = pool.stream(ids[sidx]).sigma()
         np.testing.assert_allclose(s, o.s, rtol=0, atol=SIG_TOL[1] * o.s[0])
+    pool.close()
+
+
+def _shrink_inputs():
+    # four factors and low noise: EVR(3) ~ 0.944, EVR(4 .. 9) ~ 0.9999, so with tau_shrink = 0.9995
+    # the rank steps down from 10 to 4 (one step per check) and stays; the oracle's log below
+    # asserts a margin of at least 1e-4 around both thresholds at every check.
+    A0, fm = streams.make_panel(150, 50, 4, seed=5, noise_scale=1e-4)
+    ev = streams.make_events(fm, 150, 120, mix=(0.6, 0.2, 0.2), seed=15)
+    return A0, ev
+
+
+class _MarginOracle(oracle.OracleISVD):
+    """The oracle, logging at each check how far EVR(k - 1) and EVR are from the thresholds."""
+    def _after_update(self):
+        pol = self.policy
+        if pol.check_every and (self.t + 1) % pol.check_every == 0:
+            km1 = float(np.sum(self.s[:self.k - 1] ** 2) / self.N)
+            self.margins.append(min(abs(km1 - pol.tau_shrink), abs(float(np.sum(self.s ** 2) / self.N) - pol.tau_evr)))
+        super()._after_update()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_stream_rank_shrink_matches_oracle(isvd, prec):
+    dt = np.float64 if prec == 0 else np.float32
+    A0, ev = _shrink_inputs()
+    A0 = A0.astype(dt)
+    pol = oracle.Policy(kind=oracle.POLICY_ADAPTIVE_RANK | oracle.POLICY_RANK_SHRINK, check_every=10,
+                        tau_evr=0.5, tau_shrink=0.9995, k_min=1, k_max=12)
+    o = _MarginOracle(A0.astype(np.float64), 10, tol_rel=1e-10 if prec == 0 else 3e-6, policy=pol)
+    o.margins = []
+    g = isvd.ISVD(A0, 10, k_max=16, prec=prec)
+    g.set_policy(kind=isvd.POLICY_ADAPTIVE_RANK | isvd.POLICY_RANK_SHRINK, check_every=10, tau_evr=0.5,
+                 tau_shrink=0.9995, k_min=1, k_max=12)
+    path = []
+    for e in range(len(ev)):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+            g.update_entry(int(ev.i[e]), int(ev.j[e]), float(ev.delta[e]))
+        else:
+            v = ev.vector(e).astype(dt)
+            o.apply(kd, v.astype(np.float64))
+            (g.append_row if kd == streams.ROW else g.append_col)(v)
+        mt = g.metrics(full=False)
+        assert mt["k"] == o.k and mt["r"] == o.r, e
+        if o.t % 10 == 0:
+            path.append(o.k)
+    assert min(o.margins) > 1e-4
+    assert path[:7] == [9, 8, 7, 6, 5, 4, 4]          # one step per check down to 4, then held
+    np.testing.assert_allclose(g.sigma(), o.s, rtol=0, atol=SIG_TOL[prec] * o.s[0])
+    U, s, V = g.factors()
+    R = (U.astype(np.float64) * s) @ V.astype(np.float64).T
+    assert np.linalg.norm(R - o.reconstruction()) <= SIG_TOL[prec] * np.linalg.norm(o.reconstruction())
+
+
+def test_pool_rank_shrink_matches_oracle(isvd):
+    """The pool's rank rule with its shrink side (rank_every = 10): the stream steps down to 4."""
+    A0, ev = _shrink_inputs()
+    A0 = A0.astype(np.float32)
+    f = oracle.truncated_svd(A0.astype(np.float64), 10)
+    pool = isvd.Pool(k_max=16, rank_every=10, tau_evr=0.5, tau_shrink=0.9995)
+    sid = pool.admit(A0, 10, factors=f)
+    pol = oracle.Policy(kind=oracle.POLICY_ADAPTIVE_RANK | oracle.POLICY_RANK_SHRINK, check_every=10,
+                        tau_evr=0.5, tau_shrink=0.9995, k_min=1, k_max=16)
+    o = _MarginOracle(A0.astype(np.float64), 10, tol_rel=3e-6, policy=pol, factors=f)
+    o.margins = []
+    for e in range(len(ev)):
+        kd = int(ev.kind[e])
+        if kd == streams.ENTRY:
+            pool.submit([(sid, kd, int(ev.i[e]), int(ev.j[e]), float(ev.delta[e]), 0, 0)], np.zeros(1, np.float32))
+            o.update_entry(ev.i[e], ev.j[e], ev.delta[e])
+        else:
+            v = ev.vector(e).astype(np.float32)
+            pool.submit([(sid, kd, 0, 0, 0.0, 0, v.size)], v)
+            o.apply(kd, v.astype(np.float64))
+        pool.sync()
+        mt = pool.stream(sid).metrics(full=False)
+        assert mt["k"] == o.k and mt["r"] == o.r, e
+    assert min(o.margins) > 1e-4 and o.k == 4
+    np.testing.assert_allclose(pool.stream(sid).sigma(), o.s, rtol=0, atol=SIG_TOL[1] * o.s[0])
     pool.close()
