@@ -15,6 +15,11 @@ every 250 updates, loss-of-orthogonality monitor every 256 updates. A "step" is 
 ``--batch`` consecutive events of that stream through the whole path (projection, core SVD,
 rotations, dense-A bookkeeping, policy checks, refreshes, re-orthogonalisation).
 
+Workload ``tall-200000x20000``: one dense FP32 200,000 x 20,000 stream (50-factor model plus
+N(0, 1e-4) noise, k = 64 by default, ``--k`` up to 128); a step is 100 rank-1 entry updates and one
+row append, timed with deferred rotations (``isvd_set_deferred_rotations``) and then in the plain
+form on the same handle.
+
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on the same stream.
 """
 from __future__ import annotations
@@ -49,6 +54,12 @@ WORKLOADS = {
                          "Poisson arrivals, row/col/entry 60/10/30, admission under an HBM budget (120 GB per "
                          "20,000 streams), adaptive rank (EVR < 0.9, capped at each stream's rank bucket), "
                          "continuous batching: each submit takes the requests that have arrived"),
+    "tall-200000x20000": dict(prec="fp32", m=200_000, n=20_000, f=50, noise_sd=1e-4, k=64, entries_per_append=100,
+                              delta_sd=0.005,
+                              desc="one dense FP32 200,000 x 20,000 stream from a 50-factor model plus N(0, 1e-4) "
+                                   "noise; each step = 100 rank-1 entry updates (delta sd 0.005) then one row "
+                                   "append; deferred rotations (U = U0 R_U) against the plain form on the same "
+                                   "handle; no refresh policy; orthogonality monitor every 256 updates"),
     "panel-200x50-k10": dict(prec="fp64", check_every=50, T_refresh=250, batch=200,
                              desc="200x50 factor panel (5 factors), k=10, 1000 row appends then 200 entry "
                                   "updates, FP64, periodic refresh 250, metrics every 50"),
@@ -294,6 +305,201 @@ def run_gb300(args):
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
+
+
+def _tall_steps(W, m0, n0, f, Bl, vol, steps, seed):
+    """Per step: ``entries_per_append`` entry updates (positions uniform over the current shape,
+    delta ~ N(0, delta_sd^2)) and one factor-model row; one EventStream per step."""
+    rng = np.random.default_rng(seed)
+    per = W["entries_per_append"]
+    out = []
+    m = m0
+    for _ in range(steps):
+        kind = np.full(per + 1, streams.ENTRY, np.int32)
+        kind[-1] = streams.ROW
+        ii = np.zeros(per + 1, np.int64)
+        jj = np.zeros(per + 1, np.int64)
+        dd = np.zeros(per + 1, np.float64)
+        ii[:per] = rng.integers(0, m, per)
+        jj[:per] = rng.integers(0, n0, per)
+        dd[:per] = W["delta_sd"] * rng.standard_normal(per)
+        x = Bl @ (vol * rng.standard_normal(f)) + W["noise_sd"] * rng.standard_normal(n0)
+        off = np.zeros(per + 1, np.int64)
+        length = np.zeros(per + 1, np.int64)
+        length[-1] = n0
+        m_after = np.full(per + 1, m, np.int64)
+        m_after[-1] = m + 1
+        out.append(streams.EventStream(kind, off, length, ii, jj, dd, x, m_after, np.full(per + 1, n0, np.int64)))
+        m += 1
+    return out
+
+
+def run_tall(args):
+    """One tall FP32 stream: steps of entry updates and a row append, timed with deferred
+    rotations and then in the plain form on the same handle."""
+    import torch
+
+    import paper_2605_24514_gb300 as pkg
+    from paper_2605_24514_gb300 import build as b
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    b.build()
+    W = WORKLOADS[args.workload]
+    m0, n0, f = args.m or W["m"], args.n or W["n"], W["f"]
+    k = args.k or W["k"]
+    K, Wm = args.steps, args.warmup
+    seed = rank_seed(rank)
+    rng = np.random.default_rng(seed)
+    vol = 0.02 * 0.7 ** np.arange(f)
+    Bl = rng.standard_normal((n0, f)) / np.sqrt(f)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    # A0 = F B^T + noise, drawn on the device in row chunks (inputs only; the method never runs here)
+    A0 = torch.empty(m0, n0, dtype=torch.float32, device="cuda")
+    Bt = torch.tensor(Bl.T, dtype=torch.float32, device="cuda")
+    volt = torch.tensor(vol, dtype=torch.float32, device="cuda")
+    for a in range(0, m0, 20000):
+        e = min(m0, a + 20000)
+        F = torch.randn(e - a, f, generator=gen, device="cuda") * volt
+        A0[a:e] = F @ Bt + W["noise_sd"] * torch.randn(e - a, n0, generator=gen, device="cuda")
+    del Bt
+    n_steps = 2 * Wm + 3 * K
+    steps = _tall_steps(W, m0, n0, f, Bl, vol, n_steps, seed + 1)
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = pkg.ISVD(A0, k, prec=pkg.FP32, k_max=k, stream=st.cuda_stream, seed=rank, row_cap=m0 + n_steps + 8,
+                 col_cap=n0)
+    g.sync()
+    create_s = time.perf_counter() - t0
+    del A0
+    torch.cuda.empty_cache()
+    payload = [torch.from_numpy(s.payload.astype(np.float32)).to("cuda") for s in steps]
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    B = len(steps[0])
+
+    def timed(first, count):
+        evs = []
+        for i in range(first, first + count):
+            flush.zero_()
+            st.wait_stream(torch.cuda.current_stream())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.apply_events(steps[i], payload=payload[i])
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b_) for a, b_ in evs)
+
+    # deferred form: warm-up, then the timed steps with profiling and clocks
+    g.set_deferred_rotations(True)
+    timed(0, Wm)
+    clocks = Clocks(local)
+    g.profile(True)
+    l0 = g.launches
+    clocks.start()
+    ms = timed(Wm, K)
+    clk = clocks.stop()
+    launches = g.launches - l0
+    prof = g.profile_read()
+    g.profile(False)
+    ms = reduce_max(ms, world)
+    value = world * K * B / (ms / 1e3)
+    # end to end: payload from pinned host memory, sigma read back, per step
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(steps[i].payload.astype(np.float32)).pin_memory() for i in range(Wm + K, Wm + 2 * K)]
+        g.sync()
+        t0 = time.perf_counter()
+        d2h = 0
+        for j, i in enumerate(range(Wm + K, Wm + 2 * K)):
+            g.apply_events(steps[i], payload=pinned[j].numpy())
+            d2h += g.sigma().nbytes
+        torch.cuda.synchronize()
+        el = reduce_max(time.perf_counter() - t0, world)
+        e2e = {"value": world * K * B / el, "unit": "updates/s", "h2d_bytes_per_step": int(4 * n0 + 48 * B),
+               "d2h_bytes_per_step": int(d2h // K)}
+    # plain form on the same handle
+    g.set_deferred_rotations(False)
+    timed(Wm + 2 * K, Wm)
+    ms_plain = reduce_max(timed(2 * Wm + 2 * K, K), world)
+    eu, ev_ = g.reorthogonalize(force=False)
+    if rank != 0:
+        return None
+    peak, peak_src = measured_peaks()
+    classes = {c: {"ms": round(v[0], 3), "launches": int(v[2]),
+                   "us_per_launch": round(1e3 * v[0] / v[2], 3) if v[2] else None,
+                   "GBps": round(v[1] / (v[0] * 1e6), 1) if v[0] > 0 and v[1] > 0 else None}
+               for c, v in prof.items()}
+    dom = max(prof, key=lambda c: prof[c][0])
+    r_ms, r_bytes, _ = prof["rotate"]
+    achieved = r_bytes / (r_ms * 1e6) if r_ms > 0 else 0.0
+    out = {
+        "metric": "iSVD updates/s of one tall stream, deferred rotations vs the plain form",
+        "value": round(value, 1),
+        "unit": "updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": round(ms / K, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded 50-factor model drawn on the device, update stream from the same model)",
+        "config": {"workload": args.workload, "desc": W["desc"], "m0": m0, "n0": n0, "k": k, "events_per_step": B,
+                   "form": "deferred rotations, per-update kernel launches on one CUDA stream",
+                   "plain_form_updates_per_s": round(world * K * B / (ms_plain / 1e3), 1),
+                   "speedup_vs_plain_form": round(ms_plain / ms, 3),
+                   "create_s": round(create_s, 2),
+                   "orth_err_end": [eu, ev_],
+                   "l2": "flushed between steps (256 MB device write, untimed); U, V and A exceed L2",
+                   "kernel_classes": classes, "dominant_class": dom,
+                   "parallelism": "replicas" if world > 1 else "single stream"},
+        "roofline": {"kernel": "rotate", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                     "note": "the fold and append rotations; the deferred entry updates move k x k data only"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline_tall(W, k, budget_s=args.cpu_budget)
+    return out
+
+
+def cpu_baseline_tall(W, k, budget_s=15.0):
+    """The oracle on the same step pattern at a reduced shape (20,000 x 2,000): its dense FP64 A
+    and per-update SVDs of the full shape do not fit a bounded CPU sample."""
+    import oracle
+    m0, n0, f = 20_000, 2_000, W["f"]
+    rng = np.random.default_rng(5)
+    vol = 0.02 * 0.7 ** np.arange(f)
+    Bl = rng.standard_normal((n0, f)) / np.sqrt(f)
+    A0 = (rng.standard_normal((m0, f)) * vol) @ Bl.T + W["noise_sd"] * rng.standard_normal((m0, n0))
+    A0 = A0.astype(np.float32).astype(np.float64)
+    steps = _tall_steps(W, m0, n0, f, Bl, vol, 50, 6)
+    t0 = time.perf_counter()
+    o = oracle.OracleISVD(A0, k, tol_rel=3e-6)
+    t1 = time.perf_counter()
+    n = 0
+    for sl in steps:
+        for e in range(len(sl)):
+            if sl.kind[e] == streams.ENTRY:
+                o.update_entry(sl.i[e], sl.j[e], sl.delta[e])
+            else:
+                o.append_row(sl.vector(e).astype(np.float32).astype(np.float64))
+            n += 1
+            if time.perf_counter() - t1 > budget_s:
+                break
+        if time.perf_counter() - t1 > budget_s:
+            break
+    el = time.perf_counter() - t1
+    return {"value": round(n / el, 3), "unit": "updates/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{n} events of the same step pattern on a 20,000 x 2,000 panel at k = {k} "
+                      f"(create {t1 - t0:.1f} s excluded; time budget {budget_s:.0f} s)"}
 
 
 def run_batched(args):
@@ -838,6 +1044,14 @@ def run_reference(args):
                                  "sample": sample},
                 "e2e": {"value": round(value, 3), "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
+    if args.workload.startswith("tall"):
+        cb = cpu_baseline_tall(W, args.k or W["k"], budget_s=args.cpu_budget)
+        return {"impl": "reference", "metric": "iSVD updates/s of one tall stream, deferred rotations vs the plain form",
+                "value": cb["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 50-factor model panel and updates)",
+                "config": {"workload": args.workload, "desc": W["desc"]}, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     Bref = args.ref_batch
     n_ev = (args.warmup + args.steps) * Bref
     A0, ev, k = make_stream(args.workload, seed=0, n_events=n_ev)
@@ -890,6 +1104,9 @@ def main():
     ap.add_argument("--acc-streams", type=int, default=8)
     ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests per second")
+    ap.add_argument("--m", type=int, default=0, help="tall workload: initial rows")
+    ap.add_argument("--n", type=int, default=0, help="tall workload: columns")
+    ap.add_argument("--k", type=int, default=0, help="tall workload: working rank")
     ap.add_argument("--tc-rotations", action="store_true",
                     help="batched workload: rotate rank buckets 16 and 32 on the tensor cores")
     args = ap.parse_args()
@@ -899,6 +1116,8 @@ def main():
         out = run_batched(args)
     elif args.workload == "serving":
         out = run_serving(args)
+    elif args.workload.startswith("tall"):
+        out = run_tall(args)
     else:
         out = run_gb300(args)
     if out is not None:

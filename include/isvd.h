@@ -187,6 +187,20 @@ isvd_status isvd_update_entry(isvd_t h, int64_t i, int64_t j, double delta);
  * policy step as isvd_update_entry; errors as there. */
 isvd_status isvd_update_entry_exact(isvd_t h, int64_t i, int64_t j, double delta);
 
+/* Deferred rotations for the rank-1 entry updates of Section 2.3 (the fast form of the Brand
+ * update that the paper builds on). enable = 1 keeps U = U0 R_U and V = V0 R_V with small
+ * R_U, R_V (k x k, storage precision, owned by the handle; allocated on the first enable,
+ * ENOMEM on failure): each isvd_update_entry then gathers U0[i, :] R_U and V0[j, :] R_V for its
+ * core and multiplies R_U, R_V by the core's factors, O(k^3) work on k x k data, instead of
+ * rotating the m x k and n x k factors. The next call that needs U or V (an append, the
+ * rank-increasing entry update, refresh, metrics, re-orthogonalisation, risk, get_factors)
+ * first folds U <- U0 R_U, V <- V0 R_V in one pass; enable = 0 folds and turns the mode off.
+ * Results equal those of the plain form up to rounding (the product order differs). Single
+ * streams only: EINVAL on a pool stream's handle or for enable outside {0, 1}. */
+isvd_status isvd_set_deferred_rotations(isvd_t h, int enable);
+/* 1 iff entry updates are held in R_U, R_V and not yet folded into U, V. */
+int isvd_deferred_pending(isvd_t h);
+
 /* Applies nev events in order (same semantics as the three calls above, policy included).
  * payload holds the row/column vectors, host or device memory. */
 isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload,

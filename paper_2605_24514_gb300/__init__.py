@@ -117,6 +117,8 @@ _SIGS = {
     "isvd_append_col": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "isvd_update_entry": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double]),
     "isvd_update_entry_exact": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double]),
+    "isvd_set_deferred_rotations": (C.c_int, [C.c_void_p, C.c_int]),
+    "isvd_deferred_pending": (C.c_int, [C.c_void_p]),
     "isvd_apply_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int]),
     "isvd_set_policy": (C.c_int, [C.c_void_p, C.POINTER(Policy)]),
     "isvd_refresh": (C.c_int, [C.c_void_p, C.c_int]),
@@ -244,6 +246,14 @@ class ISVD:
     def update_entry_exact(self, i, j, delta):
         """A_ij += delta in the rank-increasing form (both residual directions join the core)."""
         self._check(lib().isvd_update_entry_exact(self._h, int(i), int(j), float(delta)), "update_entry_exact")
+
+    def set_deferred_rotations(self, enable=True):
+        """Entry updates rotate small k x k factors R_U, R_V instead of U and V (isvd_set_deferred_rotations)."""
+        self._check(lib().isvd_set_deferred_rotations(self._h, 1 if enable else 0), "set_deferred_rotations")
+
+    @property
+    def deferred_pending(self):
+        return bool(lib().isvd_deferred_pending(self._h))
 
     def apply_events(self, events, payload=None):
         """Applies a ``streams.EventStream`` (payload converted to the storage type) in one call.

@@ -57,6 +57,11 @@ struct isvd_ctx {
   int r_ref = 0;
   double* p = nullptr;
   double* px = nullptr;  // rank-increasing entry update: p, q (stride kKmaxLimit + 2), alpha, beta
+  // Deferred rotations (isvd_set_deferred_rotations): U = U0 R_U, V = V0 R_V with R_U, R_V kmax x ld
+  // in the storage type; pending: entry updates have been applied to R_U, R_V and not yet to U, V.
+  void* RU = nullptr;
+  void* RV = nullptr;
+  int defer = 0, defer_pending = 0;
   double* part = nullptr;
   void* UK = nullptr;
   void* VK = nullptr;
@@ -258,8 +263,10 @@ template <typename T>
 isvd_status launch_core(isvd_ctx* h, int kind, int64_t i, int64_t j, double delta) {
   const size_t cs = core_kernel_smem<T>(h->kmax);
   const int th = core_threads(h->kmax);
+  const bool via_r = kind == kEntry && h->defer_pending;
   CK(h, core_launch<T>(kb_bucket(h->kmax), th, cs, h->stream, kind, h->st, h->sig, h->p, (T*)h->U, (T*)h->V, h->ld, i,
-                       j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld, h->px, h->tol_rel));
+                       j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld, h->px, h->tol_rel,
+                       via_r ? (const T*)h->RU : nullptr, via_r ? (const T*)h->RV : nullptr, h->ld));
   CKL(h);
   return ISVD_OK;
 }
@@ -395,11 +402,42 @@ int proj_blocks(int64_t rows) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxProjBlocks));
 }
 
+// Deferred rotations: fold the pending R_U, R_V into the tall factors, U <- U0 R_U and
+// V <- V0 R_V (one pass of the rotation kernel over both sides, rows defer_rows -> r columns).
+// Every operation that reads U or V calls this first; a no-op when nothing is pending.
+template <typename T>
+isvd_status materialize(isvd_ctx* h) {
+  if (!h->defer_pending) return ISVD_OK;
+  RotSide su{}, sv{};
+  su.X = su.Y = h->U;
+  su.rows = h->m;
+  su.ldx = su.ldy = h->ld;
+  su.R = h->RU;
+  su.ldr = h->ld;
+  su.c_in = -2;
+  su.k_out = -2;
+  sv = su;
+  sv.X = sv.Y = h->V;
+  sv.rows = h->n;
+  sv.R = h->RV;
+  prof_begin(h, ISVD_KCLASS_ROTATE, 2.0 * (h->m + h->n) * (double)h->k_host * h->es);
+  isvd_status s = launch_rotate<T>(h, su, sv, kb_bucket(h->kmax), (const T*)nullptr, h->p);
+  if (s) return s;
+  prof_end(h);
+  h->defer_pending = 0;
+  return ISVD_OK;
+}
+
+isvd_status materialize_any(isvd_ctx* h) {
+  return h->prec == ISVD_FP64 ? materialize<double>(h) : materialize<float>(h);
+}
+
 // Row append (kind kRow, x over the n columns) or column append (kind kCol, x over the m rows),
 // x already on the device. Section 2.2 Steps 1-3 / Algorithms A1, A2.
 template <typename T>
 isvd_status do_append(isvd_ctx* h, int kind, const T* x) {
   isvd_status s;
+  if ((s = materialize<T>(h))) return s;
   if (kind == kRow) {
     if ((s = ensure_rows(h, h->m + 1))) return s;
   } else {
@@ -463,12 +501,33 @@ isvd_status do_append(isvd_ctx* h, int kind, const T* x) {
   return ISVD_OK;
 }
 
-// Rank-1 entry update, Section 2.3 / Algorithm A3.
+// Rank-1 entry update, Section 2.3 / Algorithm A3. With deferred rotations on, the core gathers
+// U0[i, :] R_U and V0[j, :] R_V and its factors go into R_U, R_V (k x k products); the tall factors
+// are left alone until the next fold.
 template <typename T>
 isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
   T* U = (T*)h->U;
   T* V = (T*)h->V;
   const double kk = (double)h->k_host;
+  if (h->defer) {
+    if (!h->defer_pending) {
+      k_defer_init<T><<<std::max(1, std::min(148, h->kmax)), 256, 0, h->stream>>>((T*)h->RU, (T*)h->RV, h->ld, h->kmax,
+                                                                                 h->st);
+      CKL(h);
+      h->defer_pending = 1;
+    }
+    prof_begin(h, ISVD_KCLASS_CORE, 2.0 * kk * kk * h->es);
+    isvd_status s0 = launch_core<T>(h, kEntry, i, j, delta);
+    if (s0) return s0;
+    prof_end(h);
+    prof_begin(h, ISVD_KCLASS_ROTATE, 4.0 * kk * kk * h->es);  // R_U, R_V read and written
+    k_defer_compose<T><<<dim3((unsigned)h->kmax, 2), 128, 0, h->stream>>>((T*)h->RU, (T*)h->RV, h->ld,
+                                                                           (const T*)h->UK, (const T*)h->VK, h->ld,
+                                                                           h->st);
+    CKL(h);
+    prof_end(h);
+    return ISVD_OK;
+  }
   prof_begin(h, ISVD_KCLASS_CORE, 2.0 * kk * kk * h->es);
   isvd_status s0 = launch_core<T>(h, kEntry, i, j, delta);
   if (s0) return s0;
@@ -496,6 +555,8 @@ isvd_status do_entry(isvd_ctx* h, int64_t i, int64_t j, double delta) {
 // Q = (e_j - V q) / beta, formed row by row in the rotations.
 template <typename T>
 isvd_status do_entry_exact(isvd_ctx* h, int64_t i, int64_t j, double delta) {
+  isvd_status sm = materialize<T>(h);
+  if (sm) return sm;
   T* U = (T*)h->U;
   T* V = (T*)h->V;
   const double kk = (double)h->k_host;
@@ -805,6 +866,7 @@ isvd_status store_ref(isvd_ctx* h, int r) {
 template <typename T>
 isvd_status do_refresh(isvd_ctx* h, int store) {
   isvd_status s;
+  if ((s = materialize<T>(h))) return s;
   {
     // The working rank may have been grown on the device (novelty rule, the pool's rank rule).
     DevState ds;
@@ -862,6 +924,7 @@ isvd_status max_angle(isvd_ctx* h, const T* Q1, int64_t rows1, int r1, const T* 
 template <typename T>
 isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
   isvd_status s;
+  if ((s = materialize<T>(h))) return s;
   DevState ds;
   if ((s = read_state(h, &ds))) return s;
   const int r = ds.r;
@@ -939,6 +1002,7 @@ isvd_status do_metrics(isvd_ctx* h, int flags, isvd_metrics_t* mt) {
 template <typename T>
 isvd_status do_risk(isvd_ctx* h, const void* w, int w_dev, int flags, isvd_risk_t* out) {
   isvd_status s;
+  if ((s = materialize<T>(h))) return s;
   DevState ds;
   if ((s = read_state(h, &ds))) return s;
   const int r = ds.r;
@@ -1036,6 +1100,7 @@ isvd_status cholqr_pass(isvd_ctx* h, T* Q, int64_t rows, int r) {
 template <typename T>
 isvd_status do_reorth(isvd_ctx* h, int force, double* eu, double* ev) {
   isvd_status s;
+  if ((s = materialize<T>(h))) return s;
   DevState ds;
   if ((s = read_state(h, &ds))) return s;
   const int r = ds.r;
@@ -1281,7 +1346,7 @@ void isvd_destroy(isvd_t h) {
   cudaStreamSynchronize(h->stream);
   void* bufs[] = {h->U, h->V, h->A, h->Uref, h->st, h->sig, h->p, h->part, h->UK, h->VK, h->xbuf, h->G,
                   h->small, h->evals, h->inv, h->scal, h->info, h->Rtmp, h->Uopt, h->Vopt, h->sig_opt, h->Cbuf,
-                  h->Yb, h->Om, h->Zd, h->Rl, h->wbuf, h->riskbuf};
+                  h->Yb, h->Om, h->Zd, h->Rl, h->wbuf, h->riskbuf, h->RU, h->RV};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1332,6 +1397,31 @@ isvd_status isvd_update_entry_exact(isvd_t h, int64_t i, int64_t j, double delta
   if (s) return s;
   return h->prec == ISVD_FP64 ? after_update<double>(h) : after_update<float>(h);
 }
+
+isvd_status isvd_set_deferred_rotations(isvd_t h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return ISVD_EINVAL;
+  if (h->sticky) return (isvd_status)h->sticky;
+  if (h->orth_on_device) return fail(h, ISVD_EINVAL, "deferred rotations serve single streams, not pool streams");
+  isvd_status s;
+  if (!enable) {
+    if ((s = materialize_any(h))) return s;
+    h->defer = 0;
+    return ISVD_OK;
+  }
+  if (!h->RU) {
+    const size_t bytes = (size_t)h->kmax * h->ld * h->es;
+    if ((s = dmalloc(h, &h->RU, bytes))) return s;
+    if ((s = dmalloc(h, &h->RV, bytes))) {
+      cudaFree(h->RU);
+      h->RU = nullptr;
+      return s;
+    }
+  }
+  h->defer = 1;
+  return ISVD_OK;
+}
+
+int isvd_deferred_pending(isvd_t h) { return h ? h->defer_pending : 0; }
 
 isvd_status isvd_apply_events(isvd_t h, const isvd_event* ev, int64_t nev, const void* payload, int64_t payload_len,
                               int payload_on_device) {
@@ -1431,8 +1521,9 @@ isvd_status isvd_get_shape(isvd_t h, int64_t* m, int64_t* n, int32_t* r, int32_t
 isvd_status isvd_get_factors(isvd_t h, void* U, double* sigma, void* V, int to_device) {
   if (!h) return ISVD_EINVAL;
   DevState ds;
-  isvd_status s = read_state(h, &ds);
+  isvd_status s = (U || V) ? materialize_any(h) : ISVD_OK;
   if (s) return s;
+  if ((s = read_state(h, &ds))) return s;
   const int r = ds.r;
   const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (U) CK(h, cudaMemcpy2DAsync(U, r * h->es, h->U, h->ld * h->es, r * h->es, h->m, kind, h->stream));

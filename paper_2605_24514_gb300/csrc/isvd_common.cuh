@@ -35,7 +35,7 @@ struct DevState {
   int32_t r_in;       // rank before the last core SVD
   int32_t k_out;      // rank after it
   int32_t sweeps;     // Jacobi sweeps of the last core SVD
-  int32_t pad0;
+  int32_t defer_rows; // deferred rotations: columns of the stored U0, V0 (rows of R_U, R_V)
   double N;           // N_t = ||A_t||_F^2
   double xnorm2;      // ||x||^2 of the last append
   double rho;         // residual norm of the last append

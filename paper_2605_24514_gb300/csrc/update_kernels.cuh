@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(kProjThreads) k_proj2(const T* __restrict__ X,
 // every root), 512 for the 128 bucket (register budget).
 __host__ __device__ constexpr int core_max_threads(int kb) { return kb <= 64 ? 1024 : 512; }
 
+// Deferred rotations (RU != nullptr, kEntry only): U and V are held as U0 R_U and V0 R_V with
+// U0, V0 of defer_rows columns, so the gathered rows are U0[i, :] R_U and V0[j, :] R_V, summed in T
+// by four lanes per output.
 // kEntryX (the rank-increasing form): e_i = U p + alpha P, e_j = V q + beta Q with p = U[i, :],
 // q = V[j, :], alpha^2 = 1 - ||p||^2 and beta^2 = 1 - ||q||^2 (unit vectors against orthonormal
 // bases; a residual norm <= tol_rel counts as zero); the core is the (r+1) x (r+1) diagonal-plus-
@@ -213,17 +216,36 @@ __host__ __device__ constexpr int core_max_threads(int kb) { return kb <= 64 ? 1
 template <typename T, typename JT, int KB>
 __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevState* st, double* sig, const double* __restrict__ p, const T* U,
                        const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A, int64_t lda, T* UK,
-                       T* VKo, int ldo, double* px, double tol_rel) {
+                       T* VKo, int ldo, double* px, double tol_rel, const T* RU, const T* RV, int ldr) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* ab = reinterpret_cast<double*>(smem);
   unsigned char* core_smem = smem + (size_t)2 * (kKmaxLimit + 1) * sizeof(double);
   const int r = st->r;
   const bool entry = kind == kEntry || kind == kEntryX;
-  if (entry) {
+  if (entry && RU) {
+    const int dr = st->defer_rows;
+    const int part = threadIdx.x & 3;
+    for (int base = 0; base < 2 * r; base += (int)blockDim.x >> 2) {
+      const int o = base + ((int)threadIdx.x >> 2);
+      const bool side_v = o >= r;
+      const int c = side_v ? o - r : o;
+      T s = T(0);
+      if (o < 2 * r) {
+        const T* row = side_v ? V + ej * (int64_t)ld : U + ei * (int64_t)ld;
+        const T* R = side_v ? RV : RU;
+        for (int l = part; l < dr; l += 4) s += row[l] * R[(int64_t)l * ldr + c];
+      }
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (o < 2 * r && part == 0) ab[(side_v ? kKmaxLimit + 1 : 0) + c] = (double)s;
+    }
+  } else if (entry) {
     for (int c = threadIdx.x; c < r; c += blockDim.x) {
       ab[c] = (double)U[ei * (int64_t)ld + c];
       ab[kKmaxLimit + 1 + c] = (double)V[ej * (int64_t)ld + c];
     }
+  }
+  if (entry) {
     if (threadIdx.x == 0) {
       T* aij = A + ei * lda + ej;
       const double old = (double)*aij;
@@ -324,10 +346,10 @@ struct RotSide {
   int64_t ldx, ldy;  // row strides
   const void* R;     // c_in (+1) x k_out, row stride ldr
   int64_t ldr;
-  int c_in;          // inner dimension (excluding the z_hat row); <0: take st->r_in
+  int c_in;          // inner dimension (excluding the z_hat row); -1: take st->r_in, -2: st->defer_rows
   int zhat;          // add z_row * R[c_in, :] with z_row = (xz[row] - X[row, :] p) / rho
   int newrow;        // also write Y[rows, :] = R[c_in, :]
-  int k_out;         // <0: take st->k_out
+  int k_out;         // -1: take st->k_out, -2: st->r
   const double* colscale;  // optional per-output-column scale (1 / sigma for U = A V S^-1)
   // Residual direction of a unit vector e_zunit (rank-increasing entry update): when zrho is set,
   // z_row = ([row == zunit] - X[row, :] . zp) / *zrho replaces the append's (xz[row] - X p) / rho,
@@ -356,8 +378,8 @@ __global__ void __launch_bounds__(kRotThreads) k_rotate(RotSide s0, RotSide s1, 
   const bool first = (int)blockIdx.x < tiles0;
   const RotSide& sd = first ? s0 : s1;
   const int64_t tile = first ? blockIdx.x : blockIdx.x - tiles0;
-  const int c_in = sd.c_in >= 0 ? sd.c_in : st->r_in;
-  const int k_out = sd.k_out >= 0 ? sd.k_out : st->k_out;
+  const int c_in = sd.c_in >= 0 ? sd.c_in : sd.c_in == -2 ? st->defer_rows : st->r_in;
+  const int k_out = sd.k_out >= 0 ? sd.k_out : sd.k_out == -2 ? st->r : st->k_out;
   if (c_in > KB || k_out > KB) return;  // the host picks KB >= both; never taken
   const bool zhat = sd.zhat && (sd.zrho ? *sd.zrho > 0.0 : st->grew != 0);
   const double* zp = sd.zrho ? sd.zp : p;
@@ -433,6 +455,52 @@ __global__ void __launch_bounds__(kRotThreads) k_rotate(RotSide s0, RotSide s1, 
   }
   if (sd.newrow && tile == 0) {
     for (int j = t; j < k_out; j += kRotThreads) Y[sd.rows * sd.ldy + j] = Rs[c_in * KB + j];
+  }
+}
+
+// ---- deferred rotations (Brand's U = U0 R_U, V = V0 R_V) -------------------------------------
+//
+// The rank-1 entry update of Section 2.3 rotates both tall factors by its core factors: U' = U U_K,
+// V' = V V_K. Written as U = U0 R_U with a small R_U (rows = defer_rows, the columns of U0), the
+// update only needs R_U <- R_U U_K (O(k^3) on k x k data instead of O((m + n) k^2) on the tall
+// factors), and the gathers of the next core read U0[i, :] R_U. Everything that needs U itself
+// (appends, refresh, metrics, re-orthogonalisation, reads) first folds U <- U0 R_U in one pass of
+// the rotation kernel (c_in = -2, k_out = -2).
+
+// R_U = R_V = I of the current rank r (rows x ldr, rows >= r, zero elsewhere); defer_rows <- r.
+template <typename T>
+__global__ void __launch_bounds__(256) k_defer_init(T* RU, T* RV, int ldr, int rows, DevState* st) {
+  const int dr = st->r;
+  const int64_t total = (int64_t)rows * ldr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / ldr), c = (int)(idx - (int64_t)l * ldr);
+    const T v = (l == c && l < dr) ? T(1) : T(0);
+    RU[idx] = v;
+    RV[idx] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->defer_rows = dr;
+}
+
+// R <- R[:, :r_in] K[:r_in, :k_out] for both sides (blockIdx.y: 0 = R_U with U_K, 1 = R_V with
+// V_K), one row of R per block, in place (the row is staged before it is overwritten); columns
+// k_out .. r_in - 1 of a truncated product are cleared. Sums in T, in the order of the tall
+// rotation's.
+template <typename T>
+__global__ void __launch_bounds__(128) k_defer_compose(T* RU, T* RV, int ldr, const T* __restrict__ UK,
+                                                       const T* __restrict__ VK, int ldo, const DevState* st) {
+  __shared__ T row[kKmaxLimit + 1];
+  const int l = blockIdx.x;
+  const int dr = st->defer_rows, r_in = st->r_in, k_out = st->k_out;
+  if (l >= dr || r_in > kKmaxLimit || k_out > r_in) return;  // uniform over the block
+  T* R = blockIdx.y ? RV : RU;
+  const T* K = blockIdx.y ? VK : UK;
+  for (int c = threadIdx.x; c < r_in; c += blockDim.x) row[c] = R[(int64_t)l * ldr + c];
+  __syncthreads();
+  for (int j = threadIdx.x; j < r_in; j += blockDim.x) {
+    T s = T(0);
+    if (j < k_out)
+      for (int c = 0; c < r_in; ++c) s += row[c] * K[(int64_t)c * ldo + j];
+    R[(int64_t)l * ldr + j] = s;
   }
 }
 
