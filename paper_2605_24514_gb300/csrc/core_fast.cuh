@@ -388,44 +388,11 @@ __device__ __forceinline__ void smem_gemm_nn(int n, const float* A, const float*
   }
 }
 
-// G = X^T X for X (inner x n, column-major, column stride ld) into G (n x n, column-major),
-// 4 x 4 register blocks over the upper block triangle, mirrored.
-__device__ __forceinline__ void smem_syrk(int n, int inner, const float* X, int ld, float* G) {
-  const int nb = (n + 3) / 4;
-  const int npairs = nb * (nb + 1) / 2;
-  for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
-    int ba = 0, rem = pidx;
-    while (rem >= nb - ba) {
-      rem -= nb - ba;
-      ++ba;
-    }
-    const int bb = ba + rem;
-    const int a0 = 4 * ba, b0 = 4 * bb;
-    float acc[4][4] = {};
-    for (int l = 0; l < inner; ++l) {
-      float xa[4], xb[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        xa[q] = (a0 + q < n) ? X[(size_t)(a0 + q) * ld + l] : 0.f;
-        xb[q] = (b0 + q < n) ? X[(size_t)(b0 + q) * ld + l] : 0.f;
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] += xa[x] * xb[y];
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int a_ = a0 + x, b_ = b0 + y;
-        if (a_ < n && b_ < n) {
-          G[(size_t)b_ * n + a_] = acc[x][y];
-          G[(size_t)a_ * n + b_] = acc[x][y];
-        }
-      }
-  }
-}
+// Inner-index start of a lane in the column sweeps (the Gram products, z = Q1^T u0). The lanes of a
+// warp read columns whose starts differ by multiples of the column stride (often a multiple of 32
+// words, i.e. one bank); starting each lane's sweep over the inner index at its own offset spreads
+// the reads over the banks. The sums are the same terms in a rotated order.
+__device__ __forceinline__ int gram_rot(int inner) { return inner > 0 ? (int)(threadIdx.x & 31) % inner : 0; }
 
 // W = K V through K's structure (column-major, W is nr x nc with column stride nr). sf, xf, bf are
 // float copies of sigma, p (append) or delta * a (entry), and b (entry); rhof = rho.
@@ -469,7 +436,9 @@ __device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, con
     const int a0 = 2 * ba, b0 = 2 * bb;
     const bool a1ok = a0 + 1 < n, b1ok = b0 + 1 < n;
     float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f, q00 = 0.f, q01 = 0.f, q10 = 0.f, q11 = 0.f;
-    for (int l = 0; l < nr; ++l) {
+    const int rs = gram_rot(nr), rq = gram_rot(n);
+    for (int l0 = 0; l0 < nr; ++l0) {
+      const int l = l0 + rs < nr ? l0 + rs : l0 + rs - nr;
       const float xa0 = W[(size_t)a0 * nr + l], xa1 = a1ok ? W[(size_t)(a0 + 1) * nr + l] : 0.f;
       const float xb0 = W[(size_t)b0 * nr + l], xb1 = b1ok ? W[(size_t)(b0 + 1) * nr + l] : 0.f;
       s00 += xa0 * xb0;
@@ -477,7 +446,8 @@ __device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, con
       s10 += xa1 * xb0;
       s11 += xa1 * xb1;
     }
-    for (int l = 0; l < n; ++l) {
+    for (int l0 = 0; l0 < n; ++l0) {
+      const int l = l0 + rq < n ? l0 + rq : l0 + rq - n;
       const float xa0 = V[(size_t)a0 * n + l], xa1 = a1ok ? V[(size_t)(a0 + 1) * n + l] : 0.f;
       const float xb0 = V[(size_t)b0 * n + l], xb1 = b1ok ? V[(size_t)(b0 + 1) * n + l] : 0.f;
       q00 += xa0 * xb0;
@@ -630,10 +600,14 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
       // Second update in the eigenbasis of the first: diag(lam) + m0 z z^T (z = Q1^T u0), solved
       // as -(diag(-lam) + |m0| z z^T); ascending poles -lam_{n-1}, ..., -lam_0.
       const float sm0 = (float)s_m[5];
+      const int rot = gram_rot(n);
       for (int s_ = t; s_ < n; s_ += blockDim.x) {
         const int j = n - 1 - s_;
         float acc = 0.f;
-        for (int i = 0; i < n; ++i) acc += V[(size_t)j * n + i] * u0[i];
+        for (int i0 = 0; i0 < n; ++i0) {
+          const int i = i0 + rot < n ? i0 + rot : i0 + rot - n;
+          acc += V[(size_t)j * n + i] * u0[i];
+        }
         wv[s_] = sm0 * acc;
         dhi[s_] = -lhi[j];
         dlo[s_] = -llo[j];
@@ -691,7 +665,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
     //   lambda_i = S_ii / (1 - R_ii); E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) (i != j),
     //   E_ii = R_ii / 2.
     for (int idx = t; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx - i * n;  // E_ij stored column-major in W: W[j * n + i]
+      const int j = idx / n, i = idx - j * n;  // E_ij stored column-major in W: W[j * n + i]
       const float Rij = (i == j ? 1.f : 0.f) - Qm[(size_t)j * n + i];
       float e;
       if (i == j) {
