@@ -469,23 +469,29 @@ __device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, con
   }
 }
 
-// Largest rank bucket the fast core serves: its four n x n float matrices fit in shared memory up
-// to k_max = 115, so the 128 bucket keeps the Jacobi core (three matrices).
-constexpr int kFastCoreMaxKB = 64;
+// Largest rank bucket the fast core serves. Its work matrices V, B and W ((n + 1) x n) stay in
+// shared memory; the verification's Gram matrix Q = V^T V joins them up to the 64 bucket and
+// lives in the caller's global scratch (n x n floats, L2-resident) for the 128 bucket, where four
+// n x n float matrices would exceed the 227 KB of shared memory of a CTA.
+constexpr int kFastCoreMaxKB = 128;
+constexpr int kFastCoreQSmemMaxKB = 64;
 
 template <typename T>
 __host__ __device__ inline size_t core_fast_smem_bytes(int kmax) {
   const int n = kmax + 1;
-  // V, B (Q2 / S / E), W ((n + 1) x n), Q (n x n), 18 n floats of vectors, 3 n ints, 2 n doubles
-  return (size_t)(4 * n * n + n + 18 * n) * sizeof(float) + (size_t)n * 3 * sizeof(int) + (size_t)n * 2 * sizeof(double) +
-         256;
+  const int mats = kmax > kFastCoreQSmemMaxKB ? 3 : 4;
+  // V, B (Q2 / S / E), W ((n + 1) x n), [Q (n x n)], 18 n floats of vectors, 3 n ints, 2 n doubles
+  return (size_t)(mats * n * n + n + 18 * n) * sizeof(float) + (size_t)n * 3 * sizeof(int) +
+         (size_t)n * 2 * sizeof(double) + 256;
 }
 
 // Fast core SVD (FP32 vectors, FP64-class singular values). Returns k_out >= 0 on success, or -1
 // when the verification failed (the caller then runs the Jacobi path). Output as core_svd_cta.
+// gq: global scratch of (KB + 1)^2 floats for the Gram matrix of the 128 bucket (unused below).
 template <typename T, int KB>
 __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VKo, int ldo, double* sig_out,
-                             int* iters) {
+                             int* iters, float* gq = nullptr) {
+  constexpr bool kQGlobal = KB > kFastCoreQSmemMaxKB;
   constexpr int kTerms = (KB + 1 + kSecLanes - 1) / kSecLanes;
   const int r = in.r;
   int nr, nc;
@@ -501,7 +507,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   float* V = reinterpret_cast<float*>(smem);   // n x n
   float* B = V + (size_t)n * n;                 // n x n
   float* W = B + (size_t)n * n;                 // (n + 1) x n
-  float* vec = W + (size_t)(n + 1) * n + (size_t)n * n;  // 15 n floats (after Q, n x n)
+  float* vec = W + (size_t)(n + 1) * n + (kQGlobal ? 0 : (size_t)n * n);  // vectors (after Q when in smem)
   float* dhi = vec;
   float* dlo = vec + n;
   float* wv = vec + 2 * n;
@@ -520,6 +526,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   __shared__ float s_max[2];
   __shared__ float s_sc[4];
   if (nc < 1) return 0;
+  if (kQGlobal && gq == nullptr) return -1;
   ISVD_STAMP(0);
   for (int i = t; i < r; i += blockDim.x) {
     const ff si = ff_of(in.sig[i]);
@@ -629,7 +636,7 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   const float tol = 8.f * Eps<float>::v * sqrtf((float)(nr > n ? nr : n));
   int pass = 0;
   // S = W^T W and Q = V^T V (R = I - Q): S into B, Q into the scratch area after W.
-  float* Qm = W + (size_t)(n + 1) * n;  // n x n (reuses the tail of the work area)
+  float* Qm = kQGlobal ? gq : W + (size_t)(n + 1) * n;  // n x n
   for (; !ge; ++pass) {
     structured_kv(in, nr, n, V, W, tmp, sf, xf, bf, rhof);
     if (t < 2) s_max[t] = 0.f;

@@ -9,8 +9,8 @@ template <typename T>
 cudaError_t core_launch(int kb, int threads, size_t smem, cudaStream_t s, int kind, DevState* st, double* sig,
                         const double* p, const T* U, const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A,
                         int64_t lda, T* UK, T* VKo, int ldo, double* px, double tol_rel, const T* RU,
-                        const T* RV, int ldr) {
-#define ISVD_CORE_ARGS kind, st, sig, p, U, V, ld, ei, ej, delta, A, lda, UK, VKo, ldo, px, tol_rel, RU, RV, ldr
+                        const T* RV, int ldr, float* gq) {
+#define ISVD_CORE_ARGS kind, st, sig, p, U, V, ld, ei, ej, delta, A, lda, UK, VKo, ldo, px, tol_rel, RU, RV, ldr, gq
   switch (kb) {
     case 16: k_core<T, T, 16><<<1, threads, smem, s>>>(ISVD_CORE_ARGS); break;
     case 32: k_core<T, T, 32><<<1, threads, smem, s>>>(ISVD_CORE_ARGS); break;
@@ -34,7 +34,7 @@ cudaError_t core_set_attrs(const size_t smem[4]) {
 template cudaError_t core_launch<ISVD_CORE_T>(int, int, size_t, cudaStream_t, int, DevState*, double*, const double*,
                                               const ISVD_CORE_T*, const ISVD_CORE_T*, int, int64_t, int64_t, double,
                                               ISVD_CORE_T*, int64_t, ISVD_CORE_T*, ISVD_CORE_T*, int, double*, double,
-                                              const ISVD_CORE_T*, const ISVD_CORE_T*, int);
+                                              const ISVD_CORE_T*, const ISVD_CORE_T*, int, float*);
 template cudaError_t core_set_attrs<ISVD_CORE_T>(const size_t[4]);
 
 }  // namespace isvd

@@ -62,6 +62,7 @@ struct isvd_ctx {
   void* RU = nullptr;
   void* RV = nullptr;
   int defer = 0, defer_pending = 0;
+  float* gq = nullptr;  // (kKmaxLimit + 1)^2 floats: the 128-bucket fast core's Gram matrix
   double* part = nullptr;
   void* UK = nullptr;
   void* VK = nullptr;
@@ -266,7 +267,7 @@ isvd_status launch_core(isvd_ctx* h, int kind, int64_t i, int64_t j, double delt
   const bool via_r = kind == kEntry && h->defer_pending;
   CK(h, core_launch<T>(kb_bucket(h->kmax), th, cs, h->stream, kind, h->st, h->sig, h->p, (T*)h->U, (T*)h->V, h->ld, i,
                        j, delta, (T*)h->A, h->col_cap, (T*)h->UK, (T*)h->VK, h->ld, h->px, h->tol_rel,
-                       via_r ? (const T*)h->RU : nullptr, via_r ? (const T*)h->RV : nullptr, h->ld));
+                       via_r ? (const T*)h->RU : nullptr, via_r ? (const T*)h->RV : nullptr, h->ld, h->gq));
   CKL(h);
   return ISVD_OK;
 }
@@ -1215,6 +1216,9 @@ isvd_status create_impl(isvd_ctx* h, const void* A0, int64_t m0, int64_t n0, int
   if ((s = dmalloc(h, (void**)&h->sig, (kKmaxLimit + 2) * 8))) return s;
   if ((s = dmalloc(h, (void**)&h->p, (kKmaxLimit + 2) * 8))) return s;
   if ((s = dmalloc(h, (void**)&h->px, (2 * (kKmaxLimit + 2) + 2) * 8))) return s;
+  if (h->kmax > kFastCoreQSmemMaxKB &&
+      (s = dmalloc(h, (void**)&h->gq, (size_t)(kKmaxLimit + 1) * (kKmaxLimit + 1) * sizeof(float))))
+    return s;
   if ((s = dmalloc(h, (void**)&h->part, (size_t)kMaxProjBlocks * kPartStride * 8))) return s;
   if ((s = dmalloc(h, &h->UK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
   if ((s = dmalloc(h, &h->VK, (size_t)(kKmaxLimit + 2) * h->ld * h->es))) return s;
@@ -1346,7 +1350,7 @@ void isvd_destroy(isvd_t h) {
   cudaStreamSynchronize(h->stream);
   void* bufs[] = {h->U, h->V, h->A, h->Uref, h->st, h->sig, h->p, h->part, h->UK, h->VK, h->xbuf, h->G,
                   h->small, h->evals, h->inv, h->scal, h->info, h->Rtmp, h->Uopt, h->Vopt, h->sig_opt, h->Cbuf,
-                  h->Yb, h->Om, h->Zd, h->Rl, h->wbuf, h->riskbuf, h->RU, h->RV};
+                  h->Yb, h->Om, h->Zd, h->Rl, h->wbuf, h->riskbuf, h->RU, h->RV, h->gq};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1923,9 +1927,11 @@ isvd_status pool_set_maps(isvd_pool_ctx* p, int64_t id, const isvd_ctx* h) {
 }
 
 int64_t stream_footprint(int64_t row_cap, int64_t col_cap, int ld) {
-  // U, V, U_ref and A in FP32 plus the handle's fixed workspace.
+  // U, V, U_ref and A in FP32 plus the handle's fixed workspace (the 128 bucket's core scratch
+  // included: ld > 64).
   const int64_t fixed = (int64_t)6 * (kKmaxLimit + 1) * (kKmaxLimit + 1) * 8 + (int64_t)kMaxProjBlocks * kPartStride * 8 +
-                        (int64_t)4 * (kKmaxLimit + 2) * ld * 4;
+                        (int64_t)4 * (kKmaxLimit + 2) * ld * 4 +
+                        (ld > kFastCoreQSmemMaxKB ? (int64_t)(kKmaxLimit + 1) * (kKmaxLimit + 1) * 4 : 0);
   return (2 * row_cap * ld + col_cap * ld + row_cap * col_cap) * 4 + fixed;
 }
 

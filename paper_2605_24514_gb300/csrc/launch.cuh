@@ -16,12 +16,13 @@ struct PoolOp;
 
 // Core SVD kernel k_core<T, T, kb> (one CTA; kb = rank bucket 16/32/64/128). px and tol_rel serve
 // the rank-increasing entry update (kind kEntryX); RU, RV (row stride ldr; nullptr: none) are the
-// deferred rotations an entry update's gathers go through.
+// deferred rotations an entry update's gathers go through; gq: (kKmaxLimit + 1)^2 floats of global
+// scratch for the fast core of the 128 bucket.
 template <typename T>
 cudaError_t core_launch(int kb, int threads, size_t smem, cudaStream_t s, int kind, DevState* st, double* sig,
                         const double* p, const T* U, const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A,
                         int64_t lda, T* UK, T* VKo, int ldo, double* px, double tol_rel, const T* RU, const T* RV,
-                        int ldr);
+                        int ldr, float* gq);
 // smem[b] = dynamic shared memory of bucket 16 << b (b = 0..3).
 template <typename T>
 cudaError_t core_set_attrs(const size_t smem[4]);

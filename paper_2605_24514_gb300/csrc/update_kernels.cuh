@@ -216,7 +216,8 @@ __host__ __device__ constexpr int core_max_threads(int kb) { return kb <= 64 ? 1
 template <typename T, typename JT, int KB>
 __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevState* st, double* sig, const double* __restrict__ p, const T* U,
                        const T* V, int ld, int64_t ei, int64_t ej, double delta, T* A, int64_t lda, T* UK,
-                       T* VKo, int ldo, double* px, double tol_rel, const T* RU, const T* RV, int ldr) {
+                       T* VKo, int ldo, double* px, double tol_rel, const T* RU, const T* RV, int ldr,
+                       float* gq) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* ab = reinterpret_cast<double*>(smem);
   unsigned char* core_smem = smem + (size_t)2 * (kKmaxLimit + 1) * sizeof(double);
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(core_max_threads(KB)) k_core(int kind, DevStat
   if (sizeof(JT) < sizeof(double) && KB <= kFastCoreMaxKB && kind != kEntryX) {
     // Secular-equation core (O(k^2) roots + verification); -1 means "use the Jacobi path".
     int it = 0;
-    k_out = core_fast_cta<T, KB>(in, core_smem, UK, VKo, ldo, sig, &it);
+    k_out = core_fast_cta<T, KB>(in, core_smem, UK, VKo, ldo, sig, &it, gq);
     if (threadIdx.x == 0) s_sweeps = 100 + it;
     __syncthreads();
   }
