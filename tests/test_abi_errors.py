@@ -75,3 +75,10 @@ def test_pool_rejects_arguments_before_device_work(pkg):
         assert not h.value
     assert L.isvd_pool_create(None, C.byref(h)) == EINVAL
     assert L.isvd_pool_submit(None, None, 1, None, 0, 0) == EINVAL
+
+
+def test_deferred_rotations_reject_null_handle(pkg):
+    L = pkg.lib()
+    assert L.isvd_set_deferred_rotations(None, 1) == EINVAL
+    assert L.isvd_set_deferred_rotations(None, 0) == EINVAL
+    assert L.isvd_deferred_pending(None) == 0
