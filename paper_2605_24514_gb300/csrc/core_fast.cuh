@@ -422,6 +422,53 @@ __device__ __forceinline__ void structured_kv(const CoreIn& in, int nr, int nc, 
   __syncthreads();
 }
 
+// S = W^T W and Q = V^T V in 4 x 4 register blocks over the upper block triangles, one Gram
+// matrix per work item (half the shared-memory loads per FMA of the 2 x 2 form below; used where
+// n is large enough that the loads, not the latency of each thread's sweep, bound the products).
+__device__ __forceinline__ void smem_two_syrk4(int n, int nr, const float* W, const float* V, float* S, float* Q) {
+  const int nb = (n + 3) / 4;
+  const int npairs = nb * (nb + 1) / 2;
+  const int rs = gram_rot(nr), rq = gram_rot(n);
+  for (int pidx = threadIdx.x; pidx < 2 * npairs; pidx += blockDim.x) {
+    const bool gs = pidx < npairs;
+    int ba = 0, rem = gs ? pidx : pidx - npairs;
+    while (rem >= nb - ba) {
+      rem -= nb - ba;
+      ++ba;
+    }
+    const int bb = ba + rem;
+    const int a0 = 4 * ba, b0 = 4 * bb;
+    const float* X = gs ? W : V;
+    const int inner = gs ? nr : n;  // also the column stride of X
+    const int rot = gs ? rs : rq;
+    float acc[4][4] = {};
+    for (int l0 = 0; l0 < inner; ++l0) {
+      const int l = l0 + rot < inner ? l0 + rot : l0 + rot - inner;
+      float xa[4], xb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xa[q] = (a0 + q < n) ? X[(size_t)(a0 + q) * inner + l] : 0.f;
+        xb[q] = (b0 + q < n) ? X[(size_t)(b0 + q) * inner + l] : 0.f;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(xa[x], xb[y], acc[x][y]);
+    }
+    float* G = gs ? S : Q;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int a_ = a0 + x, b_ = b0 + y;
+        if (a_ < n && b_ < n) {
+          G[(size_t)b_ * n + a_] = acc[x][y];
+          G[(size_t)a_ * n + b_] = acc[x][y];
+        }
+      }
+  }
+}
+
 // S = W^T W and Q = V^T V together (2 x 2 register blocks over the upper block triangle).
 __device__ __forceinline__ void smem_two_syrk(int n, int nr, const float* W, const float* V, float* S, float* Q) {
   const int nb = (n + 1) / 2;
@@ -640,7 +687,8 @@ __device__ int core_fast_cta(const CoreIn& in, unsigned char* smem, T* UK, T* VK
   for (; !ge; ++pass) {
     structured_kv(in, nr, n, V, W, tmp, sf, xf, bf, rhof);
     if (t < 2) s_max[t] = 0.f;
-    smem_two_syrk(n, nr, W, V, B, Qm);
+    if (KB > kFastCoreQSmemMaxKB) smem_two_syrk4(n, nr, W, V, B, Qm);
+    else smem_two_syrk(n, nr, W, V, B, Qm);
     __syncthreads();
     float offm = 0.f, rm = 0.f;
     for (int idx = t; idx < n * n; idx += blockDim.x) {
