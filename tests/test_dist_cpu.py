@@ -43,3 +43,39 @@ def test_two_gloo_ranks_take_max_and_distinct_seeds():
 def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(3.5, 1) == 3.5
+
+
+def _seed_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    from paper_2605_24514_gb300 import streams
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    S = 4096
+    # the panel seeds the batched workload gives its streams on this rank, and a digest of a few panels
+    seeds = [bench.rank_seed(rank) * 1_000_003 + s + 1 for s in range(S)]
+    digest = [float(streams.make_panel(20, 10, 5, seed=sd)[0].sum()) for sd in seeds[:4]]
+    t = torch.tensor([min(seeds), max(seeds)] + digest, dtype=torch.float64)
+    got = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(got, t)
+    out[rank] = [g.tolist() for g in got]
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_draw_disjoint_stream_sets():
+    """Replicas shard the batched workload by rank: the streams' panel seeds of two ranks do not
+    overlap, so no stream is served twice and each rank's pool admits only its own streams."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.start_processes(_seed_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    (lo0, hi0, *d0), (lo1, hi1, *d1) = out[0]
+    assert out[0] == out[1]                       # both ranks saw the same gathered view
+    assert hi0 < lo1 or hi1 < lo0                 # disjoint seed ranges
+    assert all(a != b for a, b in zip(d0, d1))    # and different panels
