@@ -344,6 +344,9 @@ def run_tall(args):
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     b.build()
     W = WORKLOADS[args.workload]
     m0, n0, f = args.m or W["m"], args.n or W["n"], W["f"]
